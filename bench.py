@@ -1,0 +1,469 @@
+#!/usr/bin/env python
+"""Benchmark: checkerboard Monte Carlo sweeps of the 3D Heisenberg spin glass.
+
+Workload (default): L = 256 periodic lattice (16.7M spins, 470 MB of fp32
+state), one disorder sample, Gaussian J; per sweep one heat-bath sweep at
+T = 0.3 and four over-relaxation sweeps; FP64 renormalisation and FP64
+energy every 10 sweeps.  One benchmark step = 10 sweeps (ending with the
+renormalisation and the energy), so 20 steps are the 200-sweep run.
+
+Prints one JSON line.  `value` is site updates per ns (one update = one site
+visited by one heat-bath or over-relaxation pass), timed with CUDA events on
+the library's stream with the inputs resident in HBM; `e2e` is the same
+metric through the C ABI from pinned host buffers (couplings and spins in,
+energy and spins out, every step); `roofline` is the dominant kernel (the
+over-relaxation half-sweep) against the measured HBM copy bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank runs its own disorder sample (weak scaling,
+no collective on the data path); the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Bytes per site update of each kernel (fp32, float4 spins, each
+# other-colour spin and each bond read once per half-sweep):
+#   over-relaxation / Metropolis: own spin read 16 + write 16, neighbours 16, bonds 24
+#   heat-bath: own spin write 16, neighbours 16, bonds 24 (old spin not read)
+#   energy: 28 per site (all spins 16, all bonds 12); renormalisation: 32 per site
+BYTES_OR, BYTES_HB, BYTES_ENERGY, BYTES_RENORM = 72, 56, 28, 32
+
+WORKLOADS = {
+    "l256_hb_or": dict(
+        L=256, seed=3, kind="HB", T=0.3, n_or=4, hits=1, proposal="SPHERE", step=0.5, renorm_every=10,
+        energy_every=10, sweeps_per_step=10,
+        desc=("L=256 periodic 3D Heisenberg spin glass (16.7M spins, 470 MB fp32 state), 1 sample, fp32 float4 "
+              "spins + fp32 Gaussian J; per sweep 1 heat-bath (T=0.3) + 4 over-relaxation; FP64 renorm and "
+              "FP64 energy every 10 sweeps; 1 step = 10 sweeps")),
+    "l128_met_or": dict(
+        L=128, seed=2, kind="MET", T=0.5, n_or=1, hits=4, proposal="BALL", step=0.5, renorm_every=10,
+        energy_every=10, sweeps_per_step=10,
+        desc=("L=128 periodic 3D Heisenberg spin glass, 1 sample, fp32; per sweep 4-hit Metropolis (ball "
+              "proposal, step 0.5, T=0.5) + 1 over-relaxation; 1 step = 10 sweeps")),
+}
+
+# The paper's own timings (context only; other hardware, other workload):
+# over-relaxation on an L=128 lattice, fp32 (Table 2, Table 3).
+PAPER_CONTEXT = {
+    "workload": "L=128 over-relaxation sweeps, fp32 (paper Table 2)",
+    "GTX480_TEXT_upd_per_ns": round(1 / 0.63, 3),
+    "GTX480_GM_upd_per_ns": round(1 / 0.66, 3),
+    "TeslaC1060_TEXT_upd_per_ns": round(1 / 1.8, 3),
+    "i7_SSE_OpenMP_8threads_upd_per_ns": round(1 / 5.0, 3),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="l256_hb_or")
+    ap.add_argument("--kernel", choices=["auto", "global", "slab"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
+    ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int, enabled: bool = True):
+        self.device_index = device_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.enabled = enabled
+
+    def start(self):
+        if not self.enabled:
+            return
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1].split()[0]))
+                smax.append(float(parts[2].split()[0]))
+                power.append(float(parts[3].split()[0]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# Helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("hsg_sweep.cu", "hsg_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1006_2566_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel_variant: str, L: int):
+    """DRAM bytes per over-relaxation launch from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", f"or_half_sweep_{kernel_variant}_L{L}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
+    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash():
+        return None
+    return float(m_tr.group(1))
+
+
+def step_units(wl) -> int:
+    """Site updates in one step (one per site per main-update or OR pass)."""
+    passes = (1 if wl["kind"] in ("HB", "MET") else 0) + wl["n_or"]
+    return (wl["L"] ** 3) * passes * wl["sweeps_per_step"]
+
+
+def step_bytes(wl) -> int:
+    n = wl["L"] ** 3
+    main = {"HB": BYTES_HB, "MET": BYTES_OR}.get(wl["kind"], 0)
+    per_sweep = n * (main + wl["n_or"] * BYTES_OR)
+    s = wl["sweeps_per_step"]
+    extra = 0
+    if wl["energy_every"]:
+        extra += n * BYTES_ENERGY * (s // wl["energy_every"])
+    if wl["renorm_every"]:
+        extra += n * BYTES_RENORM * (s // wl["renorm_every"])
+    return per_sweep * s + extra
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args, wl):
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_1006_2566_gb300 import build
+
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1006_2566_gb300 import hsg, inputs
+
+    L = wl["L"]
+    N = L ** 3
+    kind = {"HB": hsg.HSG_HEATBATH, "MET": hsg.HSG_METROPOLIS, "NONE": hsg.HSG_NONE}[wl["kind"]]
+    proposal = {"SPHERE": hsg.HSG_PROP_SPHERE, "BALL": hsg.HSG_PROP_BALL}[wl["proposal"]]
+    kernel = {"auto": hsg.HSG_KERNEL_AUTO, "global": hsg.HSG_KERNEL_GLOBAL, "slab": hsg.HSG_KERNEL_SLAB}[args.kernel]
+    sched = hsg.schedule(kind=kind, hits=wl["hits"], proposal=proposal, step=wl["step"], n_or=wl["n_or"], T=wl["T"],
+                         renorm_every=wl["renorm_every"], energy_every=wl["energy_every"], kernel=kernel)
+    sps = wl["sweeps_per_step"]
+    stream = torch.cuda.Stream()
+    sample = rank  # weak scaling: one disorder sample per rank
+    J = inputs.gaussian_couplings(L, seed=wl["seed"], sample=sample, dtype=np.float32)
+    lat = hsg.Lattice(L, wl["seed"], sample, 0, stream)
+    lat.set_couplings(J)
+    # inputs resident in HBM from here on
+    for _ in range(args.warmup):
+        lat.sweep(sched, sps)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device(), enabled=not args.no_clocks and rank == 0)
+    clocks.start()
+    hsg.hsg_profile_reset(lat.ctx)
+    hsg.hsg_profile(lat.ctx, True)
+    n_launch0 = hsg.hsg_launch_count(lat.ctx)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for _ in range(args.steps):
+        lat.sweep(sched, sps)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t0.elapsed_time(t1)
+    launches = hsg.hsg_launch_count(lat.ctx) - n_launch0
+    per_class = {k: hsg.hsg_profile_read(lat.ctx, k) for k in range(hsg.HSG_PROF_COUNT)}
+    hsg.hsg_profile(lat.ctx, False)
+    e_last = float(lat.energy_log()[-1]) if wl["energy_every"] else float("nan")
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+
+    # ---- end to end through the C ABI, from pinned host memory -------------
+    e2e = None
+    if not args.no_e2e:
+        Jh = torch.from_numpy(J).pin_memory()
+        s_in = torch.empty(3 * N, dtype=torch.float32).pin_memory()
+        s_out = torch.empty(3 * N, dtype=torch.float32).pin_memory()
+        hsg.hsg_get_spins(lat.ctx, s_in)
+        lat.sweep_count = 0
+        for _ in range(1):  # one untimed warm-up of the host path
+            lat.set_couplings(Jh)
+            lat.set_spins(s_in)
+            lat.sweep(sched, sps)
+            lat.energy()
+            hsg.hsg_get_spins(lat.ctx, s_out)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            lat.set_couplings(Jh)  # H2D 12N bytes, synchronises
+            lat.set_spins(s_in)  # H2D 12N bytes, synchronises
+            lat.sweep(sched, sps)
+            lat.energy()  # D2H 8 bytes, synchronises
+            hsg.hsg_get_spins(lat.ctx, s_out)  # D2H 12N bytes, synchronises
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - w0) * 1e3
+        if world > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        e2e = {"value": round(world * step_units(wl) * args.steps / (e2e_ms * 1e6), 4), "unit": "spin updates/ns",
+               "h2d_bytes_per_step": int(Jh.numel() * 4 + s_in.numel() * 4),
+               "d2h_bytes_per_step": int(8 + s_out.numel() * 4), "ms_per_step": round(e2e_ms / args.steps, 4)}
+    lat.close()
+    if world > 1:
+        torch.distributed.barrier()
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    units = step_units(wl) * args.steps * world
+    value = units / (elapsed_ms * 1e6)
+    peak, peak_kind = measured_peaks()
+    or_ms, or_n = per_class[hsg.HSG_PROF_OVERRELAX]
+    hb_ms, hb_n = per_class[hsg.HSG_PROF_HEATBATH]
+    met_ms, met_n = per_class[hsg.HSG_PROF_METROPOLIS]
+    nh = N // 2
+    variant = {"auto": "global", "global": "global", "slab": "slab"}[args.kernel]
+    roof = None
+    if or_n:
+        alg = nh * BYTES_OR
+        avg_s = or_ms / or_n / 1e3
+        ach = alg / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": "over-relaxation half-sweep", "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": profiled_traffic(variant, L), "algorithmic_bytes_per_launch": alg,
+                "avg_launch_ms": round(or_ms / or_n, 5), "launches": or_n,
+                "frac_of_nominal_8TBps": round(ach / 8000.0, 4)}
+    kernels = {}
+    for name, (ms, n), bpu in (("heatbath", (hb_ms, hb_n), BYTES_HB), ("overrelax", (or_ms, or_n), BYTES_OR),
+                               ("metropolis", (met_ms, met_n), BYTES_OR)):
+        if n:
+            kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
+                             "GBps": round(nh * bpu / (ms / n / 1e3) / 1e9, 1)}
+    for name, k in (("energy", hsg.HSG_PROF_ENERGY), ("renorm", hsg.HSG_PROF_RENORM)):
+        ms, n = per_class[k]
+        if n:
+            bpu = BYTES_ENERGY if name == "energy" else BYTES_RENORM
+            kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
+                             "GBps": round(N * bpu / (ms / n / 1e3) / 1e9, 1)}
+    step_gbps = step_bytes(wl) / (elapsed_ms / args.steps / 1e3) / 1e9
+    out = {
+        "metric": "spin updates/ns", "value": round(value, 4), "unit": "spin updates/ns", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded Gaussian J (numpy), spins uniform on S^2 from Philox",
+        "config": {"workload": wl["desc"], "L": L, "sweeps_per_step": sps, "kernel": variant,
+                   "parallelism": f"samples{world}" if world > 1 else "single sample",
+                   "l2": "inputs larger than L2 (state 470 MB vs 126 MB L2), no flush" if L >= 256 else
+                         "state fits in L2"},
+        "roofline": roof,
+        "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes(wl),
+                          "achieved_GBps": round(step_gbps, 1), "frac": round(step_gbps / peak, 4)},
+        "kernels": kernels,
+        "gpu_launches": int(launches),
+        "e2e": e2e,
+        "clocks": clk,
+        "energy_per_spin_last": e_last,
+        "paper_context": PAPER_CONTEXT,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# The oracle, timed on the host cores
+# ---------------------------------------------------------------------------
+
+def _oracle_setup(wl):
+    import oracle
+    from paper_1006_2566_gb300 import inputs
+
+    oracle.build()
+    L = wl["L"]
+    J = inputs.round_to_f32(inputs.gaussian_couplings(L, seed=wl["seed"], dtype=np.float32))
+    s = oracle.init_spins(L, wl["seed"])
+    kind = {"HB": oracle.HB, "MET": oracle.MET}.get(wl["kind"], -1)
+    p = oracle.Params(key=oracle.key(wl["seed"]), sweep=0, beta=1.0 / wl["T"], step=wl["step"], hits=wl["hits"],
+                      proposal=oracle.PROP_BALL if wl["proposal"] == "BALL" else oracle.PROP_SPHERE)
+    return oracle, L, J, s, kind, p
+
+
+def _oracle_sample_sweep(oracle, L, J, s, kind, p, i0, i1):
+    """One sweep of the schedule restricted to sites [i0, i1): main update on
+    both colours, then the OR sweeps.  Returns the site updates done."""
+    n = 0
+    if kind >= 0:
+        for c in (0, 1):
+            oracle.half_sweep_range(L, J, s, kind, c, p, i0, i1)
+        n += i1 - i0
+    return n
+
+
+def cpu_baseline(wl):
+    """One full sweep of the workload's lattice by the FP64 oracle, single
+    thread (about 10-20 s)."""
+    oracle, L, J, s, kind, p = _oracle_setup(wl)
+    N = L ** 3
+    t = time.perf_counter()
+    updates = _oracle_sample_sweep(oracle, L, J, s, kind, p, 0, N)
+    for _ in range(wl["n_or"]):
+        for c in (0, 1):
+            oracle.half_sweep(L, J, s, oracle.OR, c, p)
+        updates += N
+    dt = time.perf_counter() - t
+    return {"value": round(updates / (dt * 1e9), 6), "unit": "spin updates/ns", "cores": 1, "kind": "oracle",
+            "sample": f"1 full sweep (main update + {wl['n_or']} OR) of the L={L} lattice, fp64, 1 thread",
+            "seconds": round(dt, 2)}
+
+
+def run_reference(args, wl):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    oracle, L, J, s, kind, p = _oracle_setup(wl)
+    planes = max(1, L // 16)
+    i1 = planes * L * L  # z-planes [0, planes)
+    per_step = 0
+
+    def step():
+        n = _oracle_sample_sweep(oracle, L, J, s, kind, p, 0, i1)
+        for _ in range(wl["n_or"]):
+            for c in (0, 1):
+                oracle.half_sweep_range(L, J, s, oracle.OR, c, p, 0, i1)
+            n += i1
+        return n
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        per_step = step()
+    dt = time.perf_counter() - t
+    value = per_step * args.steps / (dt * 1e9)
+    sample = (f"per step: 1 sweep (main update + {wl['n_or']} OR) of z-planes [0,{planes}) of the L={L} lattice "
+              f"({i1} sites), fp64 oracle, 1 thread")
+    out = {"impl": "reference", "metric": "spin updates/ns", "value": round(value, 6), "unit": "spin updates/ns",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt * 1e3 / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic: seeded Gaussian J, spins from Philox",
+           "config": {"workload": wl["desc"], "L": L, "kernel": "oracle"},
+           "cpu_baseline": {"value": round(value, 6), "unit": "spin updates/ns", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(value, 6), "unit": "spin updates/ns", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * hsg.h -- C ABI of libhsg: checkerboard Monte Carlo sweeps of the 3D
+ * Heisenberg spin glass on one GB300 GPU (sm_103a).
+ *
+ * Model (Bernaschi, Parisi & Parisi, "The Heisenberg spin glass model on
+ * GPU: myths and actual facts", Sec. 2, Eq. 1 and Eq. 2): unit 3-vector
+ * spins s_i on an L^3 periodic cubic lattice, Gaussian couplings J on the
+ * nearest-neighbour bonds, H = - sum over bonds J s_i . s_j (each bond
+ * counted once), local field h_i = sum over the six neighbours J_bond s_nb.
+ *
+ * Host-visible layout ("site-major", the paper's indexing, Sec. 2):
+ *   site i = x + y*L + z*L*L;
+ *   spins  float s[3*N],  s[3*i + a] = component a of site i;
+ *   J      J[3*N],        J[3*i + d] = coupling of the bond from i to
+ *                         i + e_d (d = 0, 1, 2 for +x, +y, +z), periodic.
+ * The library keeps its own colour-split copy on the device and converts
+ * on the way in and out.
+ *
+ * Conventions for every function:
+ *   - Returns HSG_OK (0) or an error code; never throws, never aborts.
+ *   - Arguments are checked on the host before anything is launched; a bad
+ *     argument returns HSG_EINVAL and leaves the context unchanged.
+ *   - Work is queued on the stream given to hsg_create, in call order.
+ *     Functions that return host data synchronise that stream; the others
+ *     are asynchronous.
+ *   - Device memory is owned by the context (stream-ordered allocations),
+ *     released by hsg_destroy.  Caller arrays are copied, never retained.
+ *   - hsg_last_error() gives a message for the last failure.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef HSG_H
+#define HSG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hsg_status;
+enum {
+  HSG_OK = 0,
+  HSG_EINVAL = 1,   /* bad argument or call order */
+  HSG_ENOMEM = 2,   /* device or pinned-host allocation failed */
+  HSG_ECUDA = 3,    /* a CUDA runtime call failed (message in hsg_last_error) */
+  HSG_ETIMEOUT = 4, /* a bounded device wait gave up */
+  HSG_EBUSY = 5     /* resource in use */
+};
+
+/* Main update of a sweep, and the update of a single half-sweep. */
+enum {
+  HSG_NONE = 0,
+  HSG_METROPOLIS = 1, /* multi-hit Metropolis (named in Sec. 2; Table 3) */
+  HSG_HEATBATH = 2,   /* heat-bath (named in Sec. 2 and Sec. 4) */
+  HSG_OVERRELAX = 3   /* over-relaxation (Sec. 4); only for hsg_half_sweep */
+};
+
+/* Metropolis proposals. */
+enum {
+  HSG_PROP_SPHERE = 0, /* s' uniform on the unit sphere */
+  HSG_PROP_BALL = 1    /* s' = (s + step*u)/|s + step*u|, u uniform in the unit ball */
+};
+
+/* Element types and memory spaces of caller arrays. */
+enum { HSG_F32 = 0, HSG_F64 = 1 };
+enum { HSG_HOST = 0, HSG_DEVICE = 1 };
+
+/* Half-sweep kernel variant. */
+enum {
+  HSG_KERNEL_AUTO = 0,   /* library's choice for the lattice size */
+  HSG_KERNEL_GLOBAL = 1, /* one thread per site, neighbours through L1/L2 */
+  HSG_KERNEL_SLAB = 2    /* z-marching tiles: other colour staged in shared memory */
+};
+
+/* Kernel classes reported by the profiler. */
+enum {
+  HSG_PROF_INIT = 0,
+  HSG_PROF_LAYOUT = 1,   /* coupling / spin layout conversion */
+  HSG_PROF_OVERRELAX = 2,
+  HSG_PROF_METROPOLIS = 3,
+  HSG_PROF_HEATBATH = 4,
+  HSG_PROF_ENERGY = 5,   /* both energy kernels */
+  HSG_PROF_RENORM = 6,
+  HSG_PROF_COUNT = 7
+};
+
+/*
+ * One sweep = the main update (`kind`) on colour 0 then colour 1, then
+ * `n_or` over-relaxation sweeps (colour 0 then colour 1 each); then the
+ * sweep counter advances by one.  After the counter advances, every
+ * `renorm_every` sweeps the spins are renormalised in FP64, and every
+ * `energy_every` sweeps E/N (FP64) is appended to the energy log, the
+ * renormalisation first.  Colour of site (x,y,z) = (x+y+z) mod 2; colour 0
+ * goes first (Sec. 4: all white spins, then all black spins).
+ *
+ * Random numbers: Philox-4x32-10 (Salmon et al., SC'11), key (k0, k1) =
+ * (seed low word, seed high word XOR (2*sample + replica)*0x9E3779B9),
+ * counter (site, sweep low word, kind<<24 | colour<<16 | hit, sweep high
+ * word) with kind 1 = init, 3 = Metropolis, 4 = heat-bath; uniform
+ * u = ((r >> 9)*2 + 1) * 2^-24.  One draw per Metropolis hit (u0, u1:
+ * direction; u2: ball radius cbrt(u2); u3: accept iff u3 < exp(-beta dE))
+ * and one per heat-bath update (u0: polar angle via
+ * 1 - cos = -log1p(u0*expm1(-2x))/x with x = beta|h|; u1: azimuth 2 pi u1
+ * in the Duff et al. (JCGT 2017) frame of h; uniform on S^2 if x < 1e-6).
+ */
+typedef struct hsg_schedule {
+  int kind;         /* HSG_NONE | HSG_METROPOLIS | HSG_HEATBATH */
+  int hits;         /* Metropolis hits per site per half-sweep, 1..65535 */
+  int proposal;     /* HSG_PROP_SPHERE | HSG_PROP_BALL */
+  float step;       /* ball-proposal scale, > 0 */
+  int n_or;         /* over-relaxation sweeps after the main update, >= 0 */
+  double T;         /* temperature, > 0; +inf allowed (beta = 0) */
+  int renorm_every; /* 0 = never, else > 0 */
+  int energy_every; /* 0 = never, else > 0 */
+  int kernel;       /* HSG_KERNEL_* */
+} hsg_schedule;
+
+typedef struct hsg_ctx hsg_ctx; /* opaque, library-owned */
+
+/*
+ * Create a lattice of side L on the current CUDA device, queued on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * Spins start uniform on S^2, drawn from Philox kind 1 at counter site i,
+ * sweep 0 (Sec. 2: unit 3-vector spins).  The sweep counter starts at 0.
+ * L must be even (the checkerboard needs it under periodic wrap) and in
+ * [4, 1624] (site indices fit 32 bits).  Couplings must be set with
+ * hsg_set_couplings before any sweep.
+ * Errors: HSG_EINVAL (out == NULL, bad L), HSG_ENOMEM, HSG_ECUDA (no
+ * device); *out is NULL on error and nothing leaks.
+ */
+hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica,
+                      void* cuda_stream);
+
+/* Release everything the context owns; waits for its stream.  NULL is a
+ * no-op returning HSG_OK. */
+hsg_status hsg_destroy(hsg_ctx* ctx);
+
+/*
+ * Set the couplings (Eq. 1: Gaussian J_ij on nearest-neighbour bonds).
+ * J: 3*N values, site-major J[3*i + d] (see top), of type `dtype`
+ * (HSG_F32 | HSG_F64) in memory space `where` (HSG_HOST | HSG_DEVICE).
+ * FP64 values are rounded to FP32 (round to nearest) on upload; all spin
+ * arithmetic is FP32.  A host array is copied before the call returns; a
+ * device array must stay valid until the stream reaches this call.
+ * Errors: HSG_EINVAL (NULL, bad dtype/where), HSG_ENOMEM, HSG_ECUDA.
+ */
+hsg_status hsg_set_couplings(hsg_ctx* ctx, const void* J, int dtype, int where);
+
+/*
+ * Run n_sweeps sweeps of `schedule` (see hsg_schedule), asynchronously on
+ * the context's stream.  n_sweeps = 0 is a no-op.
+ * Checkerboard half-sweeps follow Sec. 4 (non-interacting spins in
+ * parallel, one launch per colour); the local field is Eq. 2;
+ * over-relaxation is the reflection s' = 2 (s.h)/(h.h) h - s (Sec. 4, the
+ * energy-conserving maximal move; s unchanged when h = 0).
+ * Errors: HSG_EINVAL (bad schedule, n_sweeps < 0, couplings not set),
+ * HSG_ENOMEM (energy log growth), HSG_ECUDA.
+ */
+hsg_status hsg_sweep(hsg_ctx* ctx, const hsg_schedule* schedule, int n_sweeps);
+
+/*
+ * E/N of the current state (Eq. 1, each bond once, divided by N = L^3):
+ * per-site local fields in FP32, dot products and the deterministic
+ * two-pass sum in FP64.  Synchronises the stream.
+ * Errors: HSG_EINVAL (NULL, couplings not set), HSG_ECUDA.
+ */
+hsg_status hsg_energy(hsg_ctx* ctx, double* e_per_spin);
+
+/* Energy log written by hsg_sweep: copies min(max_n, logged) values of
+ * E/N, oldest first, into host `out` and the number logged into *n (either
+ * pointer may be NULL when max_n = 0).  Synchronises the stream. */
+hsg_status hsg_get_energy_log(hsg_ctx* ctx, double* out, int max_n, int* n);
+hsg_status hsg_clear_energy_log(hsg_ctx* ctx);
+
+/*
+ * Spins as site-major FP32 s[3*N] (see top), in memory space `where`.
+ * hsg_get_spins with HSG_HOST synchronises; with HSG_DEVICE it is queued
+ * on the stream.  hsg_set_spins stores the values as given (no
+ * normalisation).  Together with hsg_get_sweep / hsg_set_sweep this is a
+ * full checkpoint: the random numbers depend only on (key, counter), so a
+ * resumed run repeats the continuous one bit for bit.
+ */
+hsg_status hsg_get_spins(hsg_ctx* ctx, float* out, int where);
+hsg_status hsg_set_spins(hsg_ctx* ctx, const float* in, int where);
+hsg_status hsg_get_sweep(hsg_ctx* ctx, uint64_t* sweep);
+hsg_status hsg_set_sweep(hsg_ctx* ctx, uint64_t sweep);
+
+/*
+ * One half-sweep: update `update` (HSG_OVERRELAX, HSG_METROPOLIS or
+ * HSG_HEATBATH, with the temperature / hits / proposal / kernel fields of
+ * `schedule`) on every site of `colour` (0 or 1) at the current sweep
+ * counter, which is not advanced.  Used to check single half-sweeps
+ * against the oracle and to build custom schedules.
+ */
+hsg_status hsg_half_sweep(hsg_ctx* ctx, const hsg_schedule* schedule, int update, int colour);
+
+/* Renormalise every spin, s <- s/|s|, computed in FP64, stored FP32. */
+hsg_status hsg_renorm(hsg_ctx* ctx);
+
+/*
+ * Profiler: with on != 0 every kernel the context launches is bracketed
+ * by CUDA events on its stream.  hsg_profile_read synchronises, adds the
+ * elapsed time (ms) and the number of launches of class `kclass`
+ * (HSG_PROF_*) recorded since the last reset, and hsg_profile_reset
+ * clears the records.  hsg_launch_count counts every kernel launch of the
+ * context since creation, profiled or not.
+ */
+hsg_status hsg_profile(hsg_ctx* ctx, int on);
+hsg_status hsg_profile_read(hsg_ctx* ctx, int kclass, double* total_ms, uint64_t* launches);
+hsg_status hsg_profile_reset(hsg_ctx* ctx);
+hsg_status hsg_launch_count(hsg_ctx* ctx, uint64_t* launches);
+
+/* Message of the context's last failure ("" if none).  With ctx == NULL:
+ * the calling thread's last failure of a call without a context
+ * (hsg_create, hsg_philox). */
+const char* hsg_last_error(const hsg_ctx* ctx);
+const char* hsg_status_string(hsg_status s);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int hsg_version(void);
+
+/*
+ * Philox-4x32-10 stream of one key, on the device: for t < n,
+ * out[4*t + w] = word w of Philox((t, c1, c2, c3), key(seed, sample,
+ * replica)).  out: device array of 4*n uint32, queued on `cuda_stream`.
+ * The same device function feeds every update kernel; this entry point
+ * exposes it so that its words can be compared with other Philox
+ * implementations.  Errors: HSG_EINVAL (out NULL), HSG_ECUDA.
+ */
+hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint32_t n, uint32_t* out, void* cuda_stream);
+
+/*
+ * Fault injection for tests: the k-th device allocation from now (k >= 1)
+ * fails as if the device were out of memory; k = 0 disables.  Process-wide.
+ */
+hsg_status hsg_test_fail_alloc(int k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSG_H */

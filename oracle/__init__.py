@@ -86,6 +86,8 @@ def _load():
                                            ctypes.c_int, _dp, _dp]
         lib.oracle_half_sweep.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(_Params), _dp]
+        lib.oracle_half_sweep_range.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int,
+                                                ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_int64, _dp]
         lib.oracle_renorm.argtypes = [ctypes.c_int, _dp]
         lib.oracle_sweeps.argtypes = [ctypes.c_int, _dp, _dp, ctypes.POINTER(_Schedule), _u32p, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_uint64), _dp, ctypes.POINTER(ctypes.c_int)]
@@ -206,6 +208,14 @@ def half_sweep(L: int, J: np.ndarray, s: np.ndarray, upd: int, colour_: int, par
         return m
     _load().oracle_half_sweep(int(L), _d(J), _d(s), int(upd), int(colour_), ctypes.byref(p), None)
     return None
+
+
+def half_sweep_range(L: int, J: np.ndarray, s: np.ndarray, upd: int, colour_: int, params: Params, i0: int,
+                     i1: int) -> None:
+    """In-place half-sweep of the sites i0 <= i < i1 of one colour."""
+    p = params.c()
+    _load().oracle_half_sweep_range(int(L), _d(J), _d(s), int(upd), int(colour_), ctypes.byref(p), int(i0), int(i1),
+                                    None)
 
 
 def renorm(L: int, s: np.ndarray) -> None:

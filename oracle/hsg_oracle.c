@@ -326,14 +326,14 @@ void oracle_update_site(int upd, const double s[3], const double h[3], const ora
   }
 }
 
-/* One half-sweep (reading R4): every site of colour `colour` is updated
- * from the current values of the other colour.  Sites of one colour do not
- * interact, so the loop order does not change the result.  margins, if not
- * NULL, receives per site the Metropolis margin (INFINITY elsewhere). */
-void oracle_half_sweep(int L, const double* J, double* s, int upd, int colour,
-                       const oracle_params* p, double* margins) {
-  int64_t n = (int64_t)L * L * L;
-  for (int64_t i = 0; i < n; ++i) {
+/* One half-sweep (reading R4) restricted to the sites i0 <= i < i1: every
+ * site of colour `colour` in the range is updated from the current values
+ * of the other colour.  Sites of one colour do not interact, so the loop
+ * order does not change the result.  margins, if not NULL, receives per
+ * site of the range the Metropolis margin (INFINITY elsewhere). */
+void oracle_half_sweep_range(int L, const double* J, double* s, int upd, int colour,
+                             const oracle_params* p, int64_t i0, int64_t i1, double* margins) {
+  for (int64_t i = i0; i < i1; ++i) {
     if (margins) margins[i] = INFINITY;
     if (oracle_colour(L, i) != colour) continue;
     double h[3], out[3], m;
@@ -342,6 +342,12 @@ void oracle_half_sweep(int L, const double* J, double* s, int upd, int colour,
     s[3 * i] = out[0]; s[3 * i + 1] = out[1]; s[3 * i + 2] = out[2];
     if (margins) margins[i] = m;
   }
+}
+
+/* The same half-sweep over all sites. */
+void oracle_half_sweep(int L, const double* J, double* s, int upd, int colour,
+                       const oracle_params* p, double* margins) {
+  oracle_half_sweep_range(L, J, s, upd, colour, p, 0, (int64_t)L * L * L, margins);
 }
 
 /* Renormalisation: s <- s/|s| for every site. */

@@ -1,0 +1,564 @@
+// hsg_api.cu -- the C ABI declared in include/hsg.h.
+//
+// Host code only: argument checks, stream-ordered device memory, the sweep
+// schedule (which kernels run in which order), the energy log and the
+// event-based profiler.  Every step of the Monte Carlo itself runs in the
+// kernels of hsg_sweep.cu and hsg_aux.cu.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hsg.h"
+#include "hsg_device.cuh"
+#include "hsg_internal.h"
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+constexpr int kMaxL = 1624;    // L^3 < 2^32: site indices are 32-bit Philox counters
+constexpr int kElogInit = 64;
+
+thread_local std::string g_thread_error;
+int g_fail_alloc_countdown = 0;  // test hook: k-th allocation from now fails
+
+struct ProfRec {
+  int kclass;
+  cudaEvent_t start, stop;
+};
+
+}  // namespace
+
+struct hsg_ctx {
+  int L = 0, Lh = 0;
+  long long N = 0, Nh = 0;
+  uint64_t seed = 0;
+  uint32_t sample = 0, replica = 0, k0 = 0, k1 = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0, sm_count = 0;
+  float4* spins = nullptr;  // [2][Nh]
+  float* J = nullptr;       // [3][2][Nh]
+  bool have_J = false;
+  uint64_t sweep = 0;
+  void* stage = nullptr;  // site-major staging for host copies
+  size_t stage_bytes = 0;
+  double* partials = nullptr;  // energy first-pass sums
+  double* e_out = nullptr;     // hsg_energy result
+  double* elog = nullptr;      // energy log
+  int elog_cap = 0, elog_n = 0;
+  double* host_e = nullptr;  // pinned, 1 double
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> free_events;
+  uint64_t launches = 0;
+  std::string err;
+};
+
+namespace {
+
+hsg_status fail(hsg_ctx* c, hsg_status st, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_thread_error = msg;
+  return st;
+}
+
+hsg_status cuda_fail(hsg_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (e == cudaErrorMemoryAllocation) return fail(c, HSG_ENOMEM, m);
+  return fail(c, HSG_ECUDA, m);
+}
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  if (g_fail_alloc_countdown > 0 && --g_fail_alloc_countdown == 0) return cudaErrorMemoryAllocation;
+  return cudaMallocAsync(p, bytes, s);
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+cudaEvent_t take_event(hsg_ctx* c) {
+  if (!c->free_events.empty()) {
+    cudaEvent_t e = c->free_events.back();
+    c->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Run `fn` (which launches `n_kernels` kernels on the context stream),
+// bracketed by profiler events when profiling is on.
+template <typename F>
+hsg_status launch(hsg_ctx* c, int kclass, int n_kernels, const char* what, F&& fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->prof) {
+    a = take_event(c);
+    b = take_event(c);
+    if (!a || !b) return fail(c, HSG_ECUDA, "cudaEventCreate failed");
+    cudaEventRecord(a, c->stream);
+  }
+  cudaError_t e = fn();
+  if (e != cudaSuccess) {
+    if (a) c->free_events.push_back(a);
+    if (b) c->free_events.push_back(b);
+    return cuda_fail(c, e, what);
+  }
+  c->launches += (uint64_t)n_kernels;
+  if (c->prof) {
+    cudaEventRecord(b, c->stream);
+    c->recs.push_back(ProfRec{kclass, a, b});
+  }
+  return HSG_OK;
+}
+
+hsg_status ensure_stage(hsg_ctx* c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return HSG_OK;
+  dev_free(c->stage, c->stream);
+  c->stage = nullptr;
+  c->stage_bytes = 0;
+  cudaError_t e = dev_alloc(&c->stage, bytes, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "staging buffer");
+  c->stage_bytes = bytes;
+  return HSG_OK;
+}
+
+void release(hsg_ctx* c) {
+  if (!c) return;
+  cudaStream_t s = c->stream;
+  dev_free(c->spins, s);
+  dev_free(c->J, s);
+  dev_free(c->stage, s);
+  dev_free(c->partials, s);
+  dev_free(c->e_out, s);
+  dev_free(c->elog, s);
+  cudaStreamSynchronize(s);
+  if (c->host_e) cudaFreeHost(c->host_e);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.start);
+    cudaEventDestroy(r.stop);
+  }
+  for (auto e : c->free_events) cudaEventDestroy(e);
+  delete c;
+}
+
+hsg::SweepArgs sweep_args(hsg_ctx* c, int colour, float beta, float step, int hits) {
+  hsg::SweepArgs a{};
+  const int o = 1 - colour;
+  a.own = c->spins + colour * c->Nh;
+  a.oth = c->spins + o * c->Nh;
+  a.jx_own = c->J + (0 + colour) * c->Nh;
+  a.jy_own = c->J + (2 + colour) * c->Nh;
+  a.jz_own = c->J + (4 + colour) * c->Nh;
+  a.jx_oth = c->J + (0 + o) * c->Nh;
+  a.jy_oth = c->J + (2 + o) * c->Nh;
+  a.jz_oth = c->J + (4 + o) * c->Nh;
+  a.L = c->L;
+  a.Lh = c->Lh;
+  a.colour = colour;
+  a.hits = hits;
+  a.k0 = c->k0;
+  a.k1 = c->k1;
+  a.sweep_lo = (uint32_t)(c->sweep & 0xFFFFFFFFu);
+  a.sweep_hi = (uint32_t)(c->sweep >> 32);
+  a.beta = beta;
+  a.step = step;
+  return a;
+}
+
+hsg_status check_schedule(hsg_ctx* c, const hsg_schedule* s, bool need_kind) {
+  if (!s) return fail(c, HSG_EINVAL, "schedule is NULL");
+  if (need_kind && s->kind != HSG_NONE && s->kind != HSG_METROPOLIS && s->kind != HSG_HEATBATH)
+    return fail(c, HSG_EINVAL, "schedule.kind must be HSG_NONE, HSG_METROPOLIS or HSG_HEATBATH");
+  if (s->hits < 1 || s->hits > 65535) return fail(c, HSG_EINVAL, "schedule.hits must be in [1, 65535]");
+  if (s->proposal != HSG_PROP_SPHERE && s->proposal != HSG_PROP_BALL)
+    return fail(c, HSG_EINVAL, "schedule.proposal must be HSG_PROP_SPHERE or HSG_PROP_BALL");
+  if (!(s->step > 0.0f) || !std::isfinite(s->step)) return fail(c, HSG_EINVAL, "schedule.step must be finite and > 0");
+  if (s->n_or < 0) return fail(c, HSG_EINVAL, "schedule.n_or must be >= 0");
+  if (!(s->T > 0.0)) return fail(c, HSG_EINVAL, "schedule.T must be > 0 (inf allowed)");
+  if (s->renorm_every < 0 || s->energy_every < 0) return fail(c, HSG_EINVAL, "cadences must be >= 0");
+  if (s->kernel != HSG_KERNEL_AUTO && s->kernel != HSG_KERNEL_GLOBAL && s->kernel != HSG_KERNEL_SLAB)
+    return fail(c, HSG_EINVAL, "schedule.kernel must be HSG_KERNEL_AUTO, _GLOBAL or _SLAB");
+  return HSG_OK;
+}
+
+float beta_of(double T) { return std::isinf(T) ? 0.0f : (float)(1.0 / T); }
+
+int pick_variant(const hsg_ctx* c, int requested) {
+  if (requested == HSG_KERNEL_GLOBAL || requested == HSG_KERNEL_SLAB) return requested;
+  (void)c;
+  return hsg::V_GLOBAL;
+}
+
+hsg_status run_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int colour) {
+  int upd, kclass;
+  if (update == HSG_OVERRELAX) {
+    upd = hsg::U_OR;
+    kclass = HSG_PROF_OVERRELAX;
+  } else if (update == HSG_METROPOLIS) {
+    upd = s->proposal == HSG_PROP_BALL ? hsg::U_MET_BALL : hsg::U_MET_SPHERE;
+    kclass = HSG_PROF_METROPOLIS;
+  } else {
+    upd = hsg::U_HB;
+    kclass = HSG_PROF_HEATBATH;
+  }
+  const hsg::SweepArgs a = sweep_args(c, colour, beta_of(s->T), s->step, s->hits);
+  const int variant = pick_variant(c, s->kernel);
+  return launch(c, kclass, 1, "half-sweep kernel", [&] { return hsg::launch_half_sweep(upd, variant, a, c->stream); });
+}
+
+hsg_status run_energy(hsg_ctx* c, double* out_dev) {
+  return launch(c, HSG_PROF_ENERGY, 2, "energy kernels",
+                [&] { return hsg::launch_energy(c->spins, c->J, c->L, c->partials, out_dev, c->stream); });
+}
+
+hsg_status run_renorm(hsg_ctx* c) {
+  return launch(c, HSG_PROF_RENORM, 1, "renorm kernel",
+                [&] { return hsg::launch_renorm(c->spins, c->N, c->sm_count, c->stream); });
+}
+
+hsg_status grow_elog(hsg_ctx* c, int need) {
+  if (need <= c->elog_cap) return HSG_OK;
+  int cap = c->elog_cap > 0 ? c->elog_cap : kElogInit;
+  while (cap < need) cap *= 2;
+  void* p = nullptr;
+  cudaError_t e = dev_alloc(&p, sizeof(double) * (size_t)cap, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy log");
+  if (c->elog_n > 0) {
+    e = cudaMemcpyAsync(p, c->elog, sizeof(double) * (size_t)c->elog_n, cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) {
+      dev_free(p, c->stream);
+      return cuda_fail(c, e, "energy log copy");
+    }
+  }
+  dev_free(c->elog, c->stream);
+  c->elog = static_cast<double*>(p);
+  c->elog_cap = cap;
+  return HSG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica, void* cuda_stream) {
+  if (!out) return fail(nullptr, HSG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (L < 4 || L > kMaxL || (L & 1))
+    return fail(nullptr, HSG_EINVAL, "L must be even and in [4, " + std::to_string(kMaxL) + "]");
+  hsg_ctx* c = new (std::nothrow) hsg_ctx();
+  if (!c) return fail(nullptr, HSG_ENOMEM, "host allocation failed");
+  c->L = L;
+  c->Lh = L / 2;
+  c->N = (long long)L * L * L;
+  c->Nh = c->N / 2;
+  c->seed = seed;
+  c->sample = sample;
+  c->replica = replica;
+  // Key of (seed, sample, replica): low seed word, high seed word XOR the
+  // Weyl-scrambled stream number 2*sample + replica.
+  c->k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  c->k1 = (uint32_t)(seed >> 32) ^ ((2u * sample + replica) * 0x9E3779B9u);
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) {
+    hsg_status st = cuda_fail(nullptr, e, "no usable CUDA device");
+    delete c;
+    return st;
+  }
+  struct {
+    void** p;
+    size_t bytes;
+    const char* what;
+  } allocs[] = {
+      {reinterpret_cast<void**>(&c->spins), sizeof(float4) * (size_t)c->N, "spins"},
+      {reinterpret_cast<void**>(&c->J), sizeof(float) * 3 * (size_t)c->N, "couplings"},
+      {reinterpret_cast<void**>(&c->partials), sizeof(double) * hsg::energy_partials(L), "energy partials"},
+      {reinterpret_cast<void**>(&c->e_out), sizeof(double), "energy result"},
+  };
+  for (auto& a : allocs) {
+    e = dev_alloc(a.p, a.bytes, c->stream);
+    if (e != cudaSuccess) {
+      hsg_status st = cuda_fail(nullptr, e, a.what);
+      release(c);
+      return st;
+    }
+  }
+  hsg_status st = grow_elog(c, kElogInit);
+  if (st != HSG_OK) {
+    g_thread_error = c->err;
+    release(c);
+    return st;
+  }
+  e = cudaMallocHost(&c->host_e, sizeof(double));
+  if (e != cudaSuccess) {
+    c->host_e = nullptr;
+    st = cuda_fail(nullptr, e, "pinned host slot");
+    release(c);
+    return st;
+  }
+  st = launch(c, HSG_PROF_INIT, 1, "init kernel",
+              [&] { return hsg::launch_init_spins(c->spins, L, c->k0, c->k1, c->stream); });
+  if (st != HSG_OK) {
+    g_thread_error = c->err;
+    release(c);
+    return st;
+  }
+  *out = c;
+  return HSG_OK;
+}
+
+hsg_status hsg_destroy(hsg_ctx* ctx) {
+  release(ctx);
+  return HSG_OK;
+}
+
+hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!J) return fail(c, HSG_EINVAL, "J is NULL");
+  if (dtype != HSG_F32 && dtype != HSG_F64) return fail(c, HSG_EINVAL, "dtype must be HSG_F32 or HSG_F64");
+  if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
+  const bool f64 = dtype == HSG_F64;
+  const void* src = J;
+  if (where == HSG_HOST) {
+    const size_t bytes = (f64 ? sizeof(double) : sizeof(float)) * 3 * (size_t)c->N;
+    hsg_status st = ensure_stage(c, bytes);
+    if (st != HSG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(c->stage, J, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "coupling upload");
+    src = c->stage;
+  }
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling layout kernel",
+                         [&] { return hsg::launch_scatter_couplings(src, f64, c->J, c->L, c->stream); });
+  if (st != HSG_OK) return st;
+  if (where == HSG_HOST) {
+    // The caller may reuse its array as soon as we return.
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "coupling upload sync");
+  }
+  c->have_J = true;
+  return HSG_OK;
+}
+
+hsg_status hsg_sweep(hsg_ctx* c, const hsg_schedule* s, int n_sweeps) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  hsg_status st = check_schedule(c, s, true);
+  if (st != HSG_OK) return st;
+  if (n_sweeps < 0) return fail(c, HSG_EINVAL, "n_sweeps must be >= 0");
+  if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set: call hsg_set_couplings first");
+  if (s->energy_every > 0) {
+    const uint64_t end = c->sweep + (uint64_t)n_sweeps;
+    const uint64_t logged = end / (uint64_t)s->energy_every - c->sweep / (uint64_t)s->energy_every;
+    st = grow_elog(c, c->elog_n + (int)logged);
+    if (st != HSG_OK) return st;
+  }
+  for (int k = 0; k < n_sweeps; ++k) {
+    if (s->kind != HSG_NONE) {
+      for (int colour = 0; colour < 2; ++colour)
+        if ((st = run_half_sweep(c, s, s->kind, colour)) != HSG_OK) return st;
+    }
+    for (int o = 0; o < s->n_or; ++o)
+      for (int colour = 0; colour < 2; ++colour)
+        if ((st = run_half_sweep(c, s, HSG_OVERRELAX, colour)) != HSG_OK) return st;
+    c->sweep += 1;
+    if (s->renorm_every > 0 && c->sweep % (uint64_t)s->renorm_every == 0)
+      if ((st = run_renorm(c)) != HSG_OK) return st;
+    if (s->energy_every > 0 && c->sweep % (uint64_t)s->energy_every == 0) {
+      if ((st = run_energy(c, c->elog + c->elog_n)) != HSG_OK) return st;
+      c->elog_n += 1;
+    }
+  }
+  return HSG_OK;
+}
+
+hsg_status hsg_energy(hsg_ctx* c, double* e_per_spin) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!e_per_spin) return fail(c, HSG_EINVAL, "e_per_spin is NULL");
+  if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
+  hsg_status st = run_energy(c, c->e_out);
+  if (st != HSG_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(c->host_e, c->e_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy readback");
+  *e_per_spin = *c->host_e;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_energy_log(hsg_ctx* c, double* out, int max_n, int* n) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (max_n < 0 || (max_n > 0 && !out)) return fail(c, HSG_EINVAL, "bad output buffer");
+  const int k = max_n < c->elog_n ? max_n : c->elog_n;
+  cudaError_t e = cudaSuccess;
+  if (k > 0) e = cudaMemcpyAsync(out, c->elog, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "energy log readback");
+  if (n) *n = c->elog_n;
+  return HSG_OK;
+}
+
+hsg_status hsg_clear_energy_log(hsg_ctx* c) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  c->elog_n = 0;
+  return HSG_OK;
+}
+
+hsg_status hsg_get_spins(hsg_ctx* c, float* out, int where) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!out) return fail(c, HSG_EINVAL, "out is NULL");
+  if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
+  const size_t bytes = sizeof(float) * 3 * (size_t)c->N;
+  float* dst = out;
+  if (where == HSG_HOST) {
+    hsg_status st = ensure_stage(c, bytes);
+    if (st != HSG_OK) return st;
+    dst = static_cast<float*>(c->stage);
+  }
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "spin gather kernel",
+                         [&] { return hsg::launch_gather_spins(c->spins, dst, c->L, c->stream); });
+  if (st != HSG_OK) return st;
+  if (where == HSG_HOST) {
+    cudaError_t e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spin readback");
+  }
+  return HSG_OK;
+}
+
+hsg_status hsg_set_spins(hsg_ctx* c, const float* in, int where) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!in) return fail(c, HSG_EINVAL, "in is NULL");
+  if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
+  const float* src = in;
+  if (where == HSG_HOST) {
+    const size_t bytes = sizeof(float) * 3 * (size_t)c->N;
+    hsg_status st = ensure_stage(c, bytes);
+    if (st != HSG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(c->stage, in, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spin upload");
+    src = static_cast<const float*>(c->stage);
+  }
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "spin scatter kernel",
+                         [&] { return hsg::launch_scatter_spins(src, c->spins, c->L, c->stream); });
+  if (st != HSG_OK) return st;
+  if (where == HSG_HOST) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spin upload sync");
+  }
+  return HSG_OK;
+}
+
+hsg_status hsg_get_sweep(hsg_ctx* c, uint64_t* sweep) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!sweep) return fail(c, HSG_EINVAL, "sweep is NULL");
+  *sweep = c->sweep;
+  return HSG_OK;
+}
+
+hsg_status hsg_set_sweep(hsg_ctx* c, uint64_t sweep) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  c->sweep = sweep;
+  return HSG_OK;
+}
+
+hsg_status hsg_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int colour) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  hsg_status st = check_schedule(c, s, false);
+  if (st != HSG_OK) return st;
+  if (update != HSG_OVERRELAX && update != HSG_METROPOLIS && update != HSG_HEATBATH)
+    return fail(c, HSG_EINVAL, "update must be HSG_OVERRELAX, HSG_METROPOLIS or HSG_HEATBATH");
+  if (colour != 0 && colour != 1) return fail(c, HSG_EINVAL, "colour must be 0 or 1");
+  if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
+  return run_half_sweep(c, s, update, colour);
+}
+
+hsg_status hsg_renorm(hsg_ctx* c) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  return run_renorm(c);
+}
+
+hsg_status hsg_profile(hsg_ctx* c, int on) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  c->prof = on != 0;
+  return HSG_OK;
+}
+
+hsg_status hsg_profile_read(hsg_ctx* c, int kclass, double* total_ms, uint64_t* launches) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (kclass < 0 || kclass >= HSG_PROF_COUNT) return fail(c, HSG_EINVAL, "bad kernel class");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  double ms = 0.0;
+  uint64_t n = 0;
+  for (const auto& r : c->recs) {
+    if (r.kclass != kclass) continue;
+    float t = 0.0f;
+    e = cudaEventElapsedTime(&t, r.start, r.stop);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
+    ms += t;
+    n += 1;
+  }
+  if (total_ms) *total_ms = ms;
+  if (launches) *launches = n;
+  return HSG_OK;
+}
+
+hsg_status hsg_profile_reset(hsg_ctx* c) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  for (auto& r : c->recs) {
+    c->free_events.push_back(r.start);
+    c->free_events.push_back(r.stop);
+  }
+  c->recs.clear();
+  return HSG_OK;
+}
+
+hsg_status hsg_launch_count(hsg_ctx* c, uint64_t* launches) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!launches) return fail(c, HSG_EINVAL, "launches is NULL");
+  *launches = c->launches;
+  return HSG_OK;
+}
+
+const char* hsg_last_error(const hsg_ctx* c) { return c ? c->err.c_str() : g_thread_error.c_str(); }
+
+const char* hsg_status_string(hsg_status s) {
+  switch (s) {
+    case HSG_OK: return "HSG_OK";
+    case HSG_EINVAL: return "HSG_EINVAL";
+    case HSG_ENOMEM: return "HSG_ENOMEM";
+    case HSG_ECUDA: return "HSG_ECUDA";
+    case HSG_ETIMEOUT: return "HSG_ETIMEOUT";
+    case HSG_EBUSY: return "HSG_EBUSY";
+    default: return "HSG_UNKNOWN";
+  }
+}
+
+int hsg_version(void) { return kVersion; }
+
+hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t c1, uint32_t c2, uint32_t c3,
+                      uint32_t n, uint32_t* out, void* cuda_stream) {
+  if (!out) return fail(nullptr, HSG_EINVAL, "out is NULL");
+  if (reinterpret_cast<uintptr_t>(out) % 16 != 0) return fail(nullptr, HSG_EINVAL, "out must be 16-byte aligned");
+  const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+  const uint32_t k1 = (uint32_t)(seed >> 32) ^ ((2u * sample + replica) * 0x9E3779B9u);
+  cudaError_t e = hsg::launch_philox(k0, k1, c1, c2, c3, n, out, static_cast<cudaStream_t>(cuda_stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox kernel");
+  return HSG_OK;
+}
+
+hsg_status hsg_test_fail_alloc(int k) {
+  if (k < 0) return fail(nullptr, HSG_EINVAL, "k must be >= 0");
+  g_fail_alloc_countdown = k;
+  return HSG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// hsg_aux.cu -- kernels around the sweep: spin initialisation, layout
+// conversion between the site-major host layout and the colour-split device
+// layout, the FP64 energy (Eq. 1) and the FP64 renormalisation.
+#include "hsg_device.cuh"
+#include "hsg_internal.h"
+
+namespace hsg {
+namespace {
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+constexpr int ENERGY_THREADS = 256;
+constexpr int ENERGY_BLOCKS = 1024;  // fixed, so the summation order is fixed
+constexpr int FINAL_THREADS = 1024;
+
+// Spin initialisation: site i gets the sphere point of Philox counter
+// (i, 0, INIT<<24, 0).  Grid (Lh/32, L/8, 2L): blockIdx.z = 2 z + colour.
+__global__ void k_init_spins(float4* __restrict__ S, int L, uint32_t k0, uint32_t k1) {
+  const int Lh = L / 2;
+  const int xh = blockIdx.x * 32 + threadIdx.x;
+  const int y = blockIdx.y * 8 + threadIdx.y;
+  const int c = blockIdx.z & 1, z = blockIdx.z >> 1;
+  if (xh >= Lh || y >= L) return;
+  const int p = (c + y + z) & 1;
+  const uint32_t site = (uint32_t)(2 * xh + p) + (uint32_t)y * L + (uint32_t)z * L * L;
+  const uint4 r = philox4x32_10(make_uint4(site, 0u, KIND_INIT << 24, 0u), k0, k1);
+  const float3 v = sphere_point(u01(r.x), u01(r.y));
+  const long long nh = (long long)L * L * Lh;
+  S[c * nh + ((long long)z * L + y) * Lh + xh] = make_float4(v.x, v.y, v.z, 0.0f);
+}
+
+// Site-major -> colour-split couplings.  Thread per site (x, y, z).
+template <typename T>
+__global__ void k_scatter_couplings(const T* __restrict__ src, float* __restrict__ J, int L) {
+  const int x = blockIdx.x * 64 + threadIdx.x;
+  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L || y >= L) return;
+  const int Lh = L / 2;
+  const long long nh = (long long)L * L * Lh;
+  const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
+  const int c = (x + y + z) & 1;
+  const long long q = ((long long)z * L + y) * Lh + (x >> 1);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) J[(2 * d + c) * nh + q] = (float)src[3 * i + d];
+}
+
+__global__ void k_scatter_spins(const float* __restrict__ src, float4* __restrict__ S, int L) {
+  const int x = blockIdx.x * 64 + threadIdx.x;
+  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L || y >= L) return;
+  const int Lh = L / 2;
+  const long long nh = (long long)L * L * Lh;
+  const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
+  const int c = (x + y + z) & 1;
+  S[c * nh + ((long long)z * L + y) * Lh + (x >> 1)] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0f);
+}
+
+__global__ void k_gather_spins(const float4* __restrict__ S, float* __restrict__ dst, int L) {
+  const int x = blockIdx.x * 64 + threadIdx.x;
+  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L || y >= L) return;
+  const int Lh = L / 2;
+  const long long nh = (long long)L * L * Lh;
+  const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
+  const int c = (x + y + z) & 1;
+  const float4 v = S[c * nh + ((long long)z * L + y) * Lh + (x >> 1)];
+  dst[3 * i] = v.x;
+  dst[3 * i + 1] = v.y;
+  dst[3 * i + 2] = v.z;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  return v;
+}
+
+// Energy, first pass.  Every bond joins a colour-0 and a colour-1 site, so
+// sum_bonds J s_i.s_j = sum over colour-0 sites of s_i . h_i with h_i the
+// local field of Eq. 2.  h is formed in FP32 (as in the updates); the dot
+// product and every sum are FP64.  Block b writes partials[b].
+__global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const float4* __restrict__ S,
+                                                                   const float* __restrict__ J, int L,
+                                                                   double* __restrict__ partials) {
+  const uint32_t Lh = (uint32_t)L / 2;
+  const uint32_t nh = (uint32_t)L * (uint32_t)L * Lh;
+  const float4* s0 = S;
+  const float4* s1 = S + nh;
+  const float *jx0 = J, *jx1 = J + nh, *jy0 = J + 2ull * nh, *jy1 = J + 3ull * nh, *jz0 = J + 4ull * nh,
+              *jz1 = J + 5ull * nh;
+  double acc = 0.0;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nh; t += gridDim.x * blockDim.x) {
+    const int xh = (int)(t % Lh);
+    const uint32_t r = t / Lh;
+    const int y = (int)(r % (uint32_t)L), z = (int)(r / (uint32_t)L);
+    const int p = (y + z) & 1;  // colour 0
+    const long long row = (long long)r * Lh;
+    const long long q_xp = row + (p ? wrap_inc(xh, (int)Lh) : xh);
+    const long long q_xm = row + (p ? xh : wrap_dec(xh, (int)Lh));
+    const long long q_yp = ((long long)z * L + wrap_inc(y, L)) * Lh + xh;
+    const long long q_ym = ((long long)z * L + wrap_dec(y, L)) * Lh + xh;
+    const long long q_zp = ((long long)wrap_inc(z, L) * L + y) * Lh + xh;
+    const long long q_zm = ((long long)wrap_dec(z, L) * L + y) * Lh + xh;
+    const float3 h = local_field(__ldg(s1 + q_xp), __ldg(s1 + q_xm), __ldg(s1 + q_yp), __ldg(s1 + q_ym),
+                                 __ldg(s1 + q_zp), __ldg(s1 + q_zm), __ldg(jx0 + t), __ldg(jx1 + q_xm),
+                                 __ldg(jy0 + t), __ldg(jy1 + q_ym), __ldg(jz0 + t), __ldg(jz1 + q_zm));
+    const float4 s = __ldg(s0 + t);
+    acc = fma((double)s.x, (double)h.x, fma((double)s.y, (double)h.y, fma((double)s.z, (double)h.z, acc)));
+  }
+  __shared__ double warp_part[ENERGY_THREADS / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < ENERGY_THREADS / 32 ? warp_part[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+}
+
+// Energy, second pass: one block adds the partials in a fixed order and
+// writes E/N = -(sum)/N.
+__global__ void __launch_bounds__(FINAL_THREADS) k_energy_final(const double* __restrict__ partials, int n,
+                                                                double inv_n_sites, double* __restrict__ out) {
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += FINAL_THREADS) v += partials[k];
+  __shared__ double warp_part[FINAL_THREADS / 32];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = warp_part[threadIdx.x];
+    w = warp_sum(w);
+    if (threadIdx.x == 0) *out = -w * inv_n_sites;
+  }
+}
+
+// Renormalisation s <- s/|s|: |s|^2 from the exact fp64 squares of the
+// fp32 components, the reciprocal square root in fp64, the result rounded
+// once to fp32.
+__global__ void k_renorm(float4* __restrict__ S, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    float4 v = S[t];
+    const double n2 = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, (double)v.z * (double)v.z));
+    if (n2 > 0.0) {
+      const double r = rsqrt(n2);
+      v.x = (float)(v.x * r);
+      v.y = (float)(v.y * r);
+      v.z = (float)(v.z * r);
+      S[t] = v;
+    }
+  }
+}
+
+__global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n,
+                         uint4* __restrict__ out) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = philox4x32_10(make_uint4(t, c1, c2, c3), k0, k1);
+}
+
+}  // namespace
+
+cudaError_t launch_init_spins(float4* S, int L, uint32_t k0, uint32_t k1, cudaStream_t s) {
+  k_init_spins<<<dim3(cdiv(L / 2, 32), cdiv(L, 8), 2u * L), dim3(32, 8), 0, s>>>(S, L, k0, k1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s) {
+  const dim3 grid(cdiv(L, 64), cdiv(L, 4), (unsigned)L), block(64, 4);
+  if (f64)
+    k_scatter_couplings<double><<<grid, block, 0, s>>>(static_cast<const double*>(src), J, L);
+  else
+    k_scatter_couplings<float><<<grid, block, 0, s>>>(static_cast<const float*>(src), J, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_t s) {
+  k_scatter_spins<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(src, S, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s) {
+  k_gather_spins<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(S, dst, L);
+  return cudaGetLastError();
+}
+
+size_t energy_partials(int L) {
+  const long long nh = (long long)L * L * (L / 2);
+  const long long b = (nh + ENERGY_THREADS - 1) / ENERGY_THREADS;
+  return (size_t)(b < ENERGY_BLOCKS ? b : ENERGY_BLOCKS);
+}
+
+cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out, cudaStream_t s) {
+  const int nb = (int)energy_partials(L);
+  k_energy_partial<<<nb, ENERGY_THREADS, 0, s>>>(S, J, L, partials);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_energy_final<<<1, FINAL_THREADS, 0, s>>>(partials, nb, 1.0 / ((double)L * L * L), out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_renorm(float4* S, long long n, int sm_count, cudaStream_t s) {
+  const long long want = (n + 255) / 256;
+  const long long cap = (long long)sm_count * 8;
+  k_renorm<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(S, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n, uint32_t* out,
+                          cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_philox<<<cdiv(n, 256), 256, 0, s>>>(k0, k1, c1, c2, c3, n, reinterpret_cast<uint4*>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace hsg

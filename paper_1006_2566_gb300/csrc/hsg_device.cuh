@@ -1,0 +1,159 @@
+// hsg_device.cuh -- device-side building blocks of the checkerboard sweep:
+// Philox-4x32-10, the uniform map, the three site updates and the local field.
+//
+// Device layout ("colour-split"): colour c of site (x,y,z) is (x+y+z) & 1.
+// With Lh = L/2, the sites of colour c in row (y,z) have x = 2*xh + p,
+// p = (c + y + z) & 1, and are stored at q = (z*L + y)*Lh + xh of
+//   spins  float4 S[c][N/2]            (x, y, z, unused)
+//   bonds  float  J[d][c][N/2]         d = 0,1,2: bond from the site to +x,+y,+z.
+// A site of colour c finds its six neighbours in colour 1-c at
+//   x+1: xh + p (wrapped)   x-1: xh - 1 + p (wrapped)   in the same row,
+//   y+-1, z+-1: the same xh in rows (y+-1, z) and (y, z+-1).
+// Its +d bonds are J[d][c][q]; its -d bonds are the +d bonds of the -d
+// neighbours, J[d][1-c][q_-d], read at the same index as that neighbour's spin.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hsg {
+
+// Update kinds of the half-sweep kernels.
+enum UpdKind : int { U_OR = 0, U_MET_SPHERE = 1, U_MET_BALL = 2, U_HB = 3 };
+
+// Philox stream kinds (third counter word, bits 24..31).
+constexpr uint32_t KIND_INIT = 1u, KIND_MET = 3u, KIND_HB = 4u;
+
+// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the
+// 4x32 multiply/xor bijection; the key is bumped by the Weyl increments
+// between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// (2m+1) * 2^-24 with m the top 23 bits: exact in fp32, strictly inside (0,1).
+__device__ __forceinline__ float u01(uint32_t r) {
+  return __uint2float_rn(((r >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+}
+
+// Uniform point on S^2 (z = 2 u0 - 1 uniform by Archimedes' theorem).
+// 1 - z^2 = 4 u0 (1 - u0) with both factors exact in fp32.
+__device__ __forceinline__ float3 sphere_point(float u0, float u1) {
+  const float z = fmaf(2.0f, u0, -1.0f);
+  const float rho = 2.0f * sqrtf(u0 * (1.0f - u0));
+  float s, c;
+  sincospif(2.0f * u1, &s, &c);
+  return make_float3(rho * c, rho * s, z);
+}
+
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+
+// Over-relaxation: reflection of s about h, s' = 2 (s.h)/(h.h) h - s;
+// unchanged when h = 0.
+__device__ __forceinline__ float3 update_or(float3 s, float3 h) {
+  const float hh = dot3(h, h);
+  if (hh == 0.0f) return s;
+  const float f = 2.0f * dot3(s, h) / hh;
+  return make_float3(fmaf(f, h.x, -s.x), fmaf(f, h.y, -s.y), fmaf(f, h.z, -s.z));
+}
+
+// Multi-hit Metropolis at fixed field h.  Hit j uses the Philox draw at
+// counter (site, sweep_lo, MET<<24 | colour<<16 | j, sweep_hi).  The site
+// energy in the field is -s.h, dE = -(s' - s).h, accept iff u3 < exp(-beta dE).
+template <bool BALL>
+__device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t site, uint32_t colour,
+                                                    uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
+                                                    uint32_t k1, float beta, float step, int hits) {
+  for (int j = 0; j < hits; ++j) {
+    const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_MET << 24) | (colour << 16) | (uint32_t)j,
+                                             sweep_hi),
+                                  k0, k1);
+    const float3 d = sphere_point(u01(r.x), u01(r.y));
+    float3 p;
+    if (BALL) {
+      const float a = step * cbrtf(u01(r.z));
+      const float3 v = make_float3(fmaf(a, d.x, s.x), fmaf(a, d.y, s.y), fmaf(a, d.z, s.z));
+      const float n2 = dot3(v, v);
+      if (n2 == 0.0f) continue;  // no direction: rejected
+      const float inv = 1.0f / sqrtf(n2);
+      p = make_float3(v.x * inv, v.y * inv, v.z * inv);
+    } else {
+      p = d;
+    }
+    const float de = -dot3(make_float3(p.x - s.x, p.y - s.y, p.z - s.z), h);
+    if (u01(r.w) < expf(-beta * de)) s = p;
+  }
+  return s;
+}
+
+// Heat-bath: s' from the density prop. to exp(beta s'.h) on S^2.  With
+// x = beta|h|, 1 - cos(theta) = -log1p(u0 expm1(-2x))/x inverts the CDF of
+// cos(theta); the azimuth 2 pi u1 is taken in the orthonormal frame of
+// h/|h| built as in Duff et al., "Building an Orthonormal Basis,
+// Revisited" (JCGT 2017).  Uniform on S^2 when x < 1e-6.
+__device__ __forceinline__ float3 update_heatbath(float3 h, uint32_t site, uint32_t colour, uint32_t sweep_lo,
+                                                  uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta) {
+  const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_HB << 24) | (colour << 16), sweep_hi), k0, k1);
+  const float u0 = u01(r.x), u1 = u01(r.y);
+  const float hn = sqrtf(dot3(h, h));
+  const float x = beta * hn;
+  if (!(x >= 1e-6f)) return sphere_point(u0, u1);
+  const float inv = 1.0f / hn;
+  const float3 n = make_float3(h.x * inv, h.y * inv, h.z * inv);
+  float sv = -log1pf(u0 * expm1f(-2.0f * x)) / x;
+  sv = fminf(fmaxf(sv, 0.0f), 2.0f);
+  const float ct = 1.0f - sv;
+  const float st = sqrtf(fmaxf(sv * (2.0f - sv), 0.0f));
+  float sp, cp;
+  sincospif(2.0f * u1, &sp, &cp);
+  const float sign = copysignf(1.0f, n.z);
+  const float a = -1.0f / (sign + n.z);
+  const float b = n.x * n.y * a;
+  const float3 e1 = make_float3(fmaf(sign * n.x * n.x, a, 1.0f), sign * b, -sign * n.x);
+  const float3 e2 = make_float3(b, fmaf(n.y * n.y, a, sign), -n.y);
+  const float c1 = st * cp, c2 = st * sp;
+  return make_float3(fmaf(ct, n.x, fmaf(c1, e1.x, c2 * e2.x)), fmaf(ct, n.y, fmaf(c1, e1.y, c2 * e2.y)),
+                     fmaf(ct, n.z, fmaf(c1, e1.z, c2 * e2.z)));
+}
+
+// Local field from the six neighbour spins and bonds (Eq. 2):
+// h = sum_k J_k s_k in the order +x, -x, +y, -y, +z, -z.
+__device__ __forceinline__ float3 local_field(float4 sxp, float4 sxm, float4 syp, float4 sym, float4 szp, float4 szm,
+                                              float jxp, float jxm, float jyp, float jym, float jzp, float jzm) {
+  float3 h;
+  h.x = fmaf(jzm, szm.x, fmaf(jzp, szp.x, fmaf(jym, sym.x, fmaf(jyp, syp.x, fmaf(jxm, sxm.x, jxp * sxp.x)))));
+  h.y = fmaf(jzm, szm.y, fmaf(jzp, szp.y, fmaf(jym, sym.y, fmaf(jyp, syp.y, fmaf(jxm, sxm.y, jxp * sxp.y)))));
+  h.z = fmaf(jzm, szm.z, fmaf(jzp, szp.z, fmaf(jym, sym.z, fmaf(jyp, syp.z, fmaf(jxm, sxm.z, jxp * sxp.z)))));
+  return h;
+}
+
+// Site update of kind U given the old spin s (unused by the heat-bath).
+template <int U>
+__device__ __forceinline__ float3 update_site(float3 s, float3 h, uint32_t site, uint32_t colour, uint32_t sweep_lo,
+                                              uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta, float step,
+                                              int hits) {
+  if constexpr (U == U_OR) {
+    return update_or(s, h);
+  } else if constexpr (U == U_MET_SPHERE) {
+    return update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  } else if constexpr (U == U_MET_BALL) {
+    return update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  } else {
+    return update_heatbath(h, site, colour, sweep_lo, sweep_hi, k0, k1, beta);
+  }
+}
+
+__device__ __forceinline__ int wrap_inc(int v, int n) { return v + 1 == n ? 0 : v + 1; }
+__device__ __forceinline__ int wrap_dec(int v, int n) { return v == 0 ? n - 1 : v - 1; }
+
+}  // namespace hsg

@@ -1,0 +1,55 @@
+// hsg_internal.h -- host-side interface between the C-ABI layer and the
+// kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hsg {
+
+// Arguments of one half-sweep (see hsg_device.cuh for the layout).
+struct SweepArgs {
+  float4* own;          // spins of the colour being updated
+  const float4* oth;    // spins of the other colour (read only)
+  const float* jx_own;  // +x / +y / +z bonds of the updated colour
+  const float* jy_own;
+  const float* jz_own;
+  const float* jx_oth;  // +x / +y / +z bonds of the other colour
+  const float* jy_oth;
+  const float* jz_oth;
+  int L, Lh, colour, hits;
+  uint32_t k0, k1, sweep_lo, sweep_hi;
+  float beta, step;
+};
+
+// Kernel variants (values match HSG_KERNEL_*).
+enum Variant : int { V_AUTO = 0, V_GLOBAL = 1, V_SLAB = 2 };
+
+// Half-sweep of update kind `upd` (UpdKind) with kernel `variant`
+// (V_GLOBAL or V_SLAB).  One kernel launch.
+cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, cudaStream_t s);
+
+// Spin initialisation: S[2][N/2] from Philox kind INIT.  One launch.
+cudaError_t launch_init_spins(float4* S, int L, uint32_t k0, uint32_t k1, cudaStream_t s);
+
+// Site-major -> colour-split couplings (src: 3N fp32 or fp64).  One launch.
+cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s);
+
+// Site-major fp32 spins <-> colour-split float4 spins.  One launch each.
+cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_t s);
+cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s);
+
+// Energy: number of FP64 partial sums the first pass writes, and the
+// two-pass E/N into *out (device).  Two launches.
+size_t energy_partials(int L);
+cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out, cudaStream_t s);
+
+// FP64 renormalisation of n float4 spins.  One launch.
+cudaError_t launch_renorm(float4* S, long long n, int sm_count, cudaStream_t s);
+
+// Philox words for counters (t, c1, c2, c3), t < n.  One launch.
+cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n, uint32_t* out,
+                          cudaStream_t s);
+
+}  // namespace hsg

@@ -1,0 +1,153 @@
+// hsg_sweep.cu -- checkerboard half-sweep kernels (Sec. 4: the sites of one
+// colour do not interact, so a half-sweep updates all of them in parallel
+// from the other colour; one launch per colour keeps the two colours
+// ordered).
+//
+// Two variants over the colour-split layout of hsg_device.cuh:
+//   global : one thread per updated site; the six neighbours come through
+//            L1/L2 (the lattice is streamed once per half-sweep from HBM).
+//   slab   : a CTA owns a (32 xh) x (8 y) column tile and marches up a chunk
+//            of z planes.  The other colour's plane z (with a one-site halo)
+//            is staged in shared memory for the x and y neighbours; planes
+//            z-1 and z+1 stay in registers, so each other-colour spin is
+//            read from memory about once per half-sweep.
+#include "hsg_device.cuh"
+#include "hsg_internal.h"
+
+namespace hsg {
+namespace {
+
+inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
+
+__device__ __forceinline__ uint32_t site_index(int xh, int p, int y, int z, int L) {
+  return (uint32_t)(2 * xh + p) + (uint32_t)y * (uint32_t)L + (uint32_t)z * (uint32_t)L * (uint32_t)L;
+}
+
+// ---------------------------------------------------------------------------
+// Global variant.
+// ---------------------------------------------------------------------------
+constexpr int GX = 32, GY = 8;
+
+template <int U>
+__global__ void __launch_bounds__(GX* GY) k_half_sweep_global(const SweepArgs a) {
+  const int xh = blockIdx.x * GX + threadIdx.x;
+  const int y = blockIdx.y * GY + threadIdx.y;
+  const int z = blockIdx.z;
+  const int L = a.L, Lh = a.Lh;
+  if (xh >= Lh || y >= L) return;
+  const int p = (a.colour + y + z) & 1;  // x = 2*xh + p
+  const long long row = ((long long)z * L + y) * Lh;
+  const long long q = row + xh;
+  const long long q_xp = row + (p ? wrap_inc(xh, Lh) : xh);
+  const long long q_xm = row + (p ? xh : wrap_dec(xh, Lh));
+  const long long q_yp = ((long long)z * L + wrap_inc(y, L)) * Lh + xh;
+  const long long q_ym = ((long long)z * L + wrap_dec(y, L)) * Lh + xh;
+  const long long q_zp = ((long long)wrap_inc(z, L) * L + y) * Lh + xh;
+  const long long q_zm = ((long long)wrap_dec(z, L) * L + y) * Lh + xh;
+
+  const float4 sxp = __ldg(a.oth + q_xp), sxm = __ldg(a.oth + q_xm);
+  const float4 syp = __ldg(a.oth + q_yp), sym = __ldg(a.oth + q_ym);
+  const float4 szp = __ldg(a.oth + q_zp), szm = __ldg(a.oth + q_zm);
+  const float jxp = __ldg(a.jx_own + q), jxm = __ldg(a.jx_oth + q_xm);
+  const float jyp = __ldg(a.jy_own + q), jym = __ldg(a.jy_oth + q_ym);
+  const float jzp = __ldg(a.jz_own + q), jzm = __ldg(a.jz_oth + q_zm);
+  float3 s = make_float3(0.0f, 0.0f, 0.0f);
+  if constexpr (U != U_HB) {
+    const float4 o = a.own[q];
+    s = make_float3(o.x, o.y, o.z);
+  }
+  const float3 h = local_field(sxp, sxm, syp, sym, szp, szm, jxp, jxm, jyp, jym, jzp, jzm);
+  const float3 t = update_site<U>(s, h, site_index(xh, p, y, z, L), (uint32_t)a.colour, a.sweep_lo, a.sweep_hi,
+                                  a.k0, a.k1, a.beta, a.step, a.hits);
+  a.own[q] = make_float4(t.x, t.y, t.z, 0.0f);
+}
+
+// ---------------------------------------------------------------------------
+// Slab variant.
+// ---------------------------------------------------------------------------
+constexpr int TX = 32, TY = 8, ZC = 16;
+
+template <int U>
+__global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
+  // Two buffers of the other colour's plane tile: slot (r, c) holds the site
+  // ((x0 + c - 1) mod Lh, (y0 + r - 1) mod L); the corners are unused.
+  __shared__ float4 plane[2][TY + 2][TX + 2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int L = a.L, Lh = a.Lh;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * ZC;
+  const int z1 = min(z0 + ZC, L);
+  const int xh = x0 + tx, y = y0 + ty;
+  const bool valid = xh < Lh && y < L;
+  // Threads past the lattice edge fill their slot with the periodic image.
+  const int xw = xh % Lh, yw = y % L;
+  const int x_left = (x0 + Lh - 1) % Lh, x_right = (x0 + TX) % Lh;
+  const int y_top = (y0 + L - 1) % L, y_bot = (y0 + TY) % L;
+  const long long plane_sz = (long long)L * Lh;
+  const long long col = (long long)yw * Lh + xw;  // this slot's offset in a plane
+
+  int zprev = wrap_dec(z0, L);
+  float4 s_zm = __ldg(a.oth + zprev * plane_sz + col);
+  float4 s_z = __ldg(a.oth + z0 * plane_sz + col);
+  float jzm = valid ? __ldg(a.jz_oth + zprev * plane_sz + col) : 0.0f;
+
+  for (int z = z0; z < z1; ++z) {
+    const int zn = wrap_inc(z, L);
+    const float4 s_zp = __ldg(a.oth + zn * plane_sz + col);
+    const long long pz = (long long)z * plane_sz;
+    float4(*buf)[TX + 2] = plane[(z - z0) & 1];
+    buf[ty + 1][tx + 1] = s_z;
+    if (ty == 0) buf[0][tx + 1] = __ldg(a.oth + pz + (long long)y_top * Lh + xw);
+    if (ty == 1) buf[TY + 1][tx + 1] = __ldg(a.oth + pz + (long long)y_bot * Lh + xw);
+    if (tx == 0) buf[ty + 1][0] = __ldg(a.oth + pz + (long long)yw * Lh + x_left);
+    if (tx == 1) buf[ty + 1][TX + 1] = __ldg(a.oth + pz + (long long)yw * Lh + x_right);
+    __syncthreads();
+    if (valid) {
+      const int p = (a.colour + y + z) & 1;
+      const long long row = pz + (long long)y * Lh;
+      const long long q = row + xh;
+      const float jxp = __ldg(a.jx_own + q), jyp = __ldg(a.jy_own + q), jzp = __ldg(a.jz_own + q);
+      const float jxm = __ldg(a.jx_oth + row + (p ? xh : wrap_dec(xh, Lh)));
+      const float jym = __ldg(a.jy_oth + pz + (long long)wrap_dec(y, L) * Lh + xh);
+      const float jz_here = __ldg(a.jz_oth + q);  // -z bond of the site above
+      float3 s = make_float3(0.0f, 0.0f, 0.0f);
+      if constexpr (U != U_HB) {
+        const float4 o = a.own[q];
+        s = make_float3(o.x, o.y, o.z);
+      }
+      const float3 h = local_field(buf[ty + 1][tx + 1 + p], buf[ty + 1][tx + p], buf[ty + 2][tx + 1],
+                                   buf[ty][tx + 1], s_zp, s_zm, jxp, jxm, jyp, jym, jzp, jzm);
+      const float3 t = update_site<U>(s, h, site_index(xh, p, y, z, L), (uint32_t)a.colour, a.sweep_lo,
+                                      a.sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
+      a.own[q] = make_float4(t.x, t.y, t.z, 0.0f);
+      jzm = jz_here;
+    }
+    s_zm = s_z;
+    s_z = s_zp;
+  }
+}
+
+template <int U>
+cudaError_t launch_kind(int variant, const SweepArgs& a, cudaStream_t s) {
+  if (variant == V_SLAB) {
+    const dim3 grid(cdiv(a.Lh, TX), cdiv(a.L, TY), cdiv(a.L, ZC));
+    k_half_sweep_slab<U><<<grid, dim3(TX, TY), 0, s>>>(a);
+  } else {
+    const dim3 grid(cdiv(a.Lh, GX), cdiv(a.L, GY), (unsigned)a.L);
+    k_half_sweep_global<U><<<grid, dim3(GX, GY), 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, cudaStream_t s) {
+  switch (upd) {
+    case U_OR: return launch_kind<U_OR>(variant, a, s);
+    case U_MET_SPHERE: return launch_kind<U_MET_SPHERE>(variant, a, s);
+    case U_MET_BALL: return launch_kind<U_MET_BALL>(variant, a, s);
+    case U_HB: return launch_kind<U_HB>(variant, a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace hsg

@@ -1,0 +1,313 @@
+"""ctypes binding of libhsg (the C ABI in ``include/hsg.h``).
+
+Argument marshalling only: every step of the Monte Carlo runs in the CUDA
+kernels of ``libhsg.so``.  The functions keep the C names; ``Lattice`` wraps
+a context for convenience.  Importing this module loads the library and
+raises ``ImportError`` if it has not been built: there is no fallback.
+
+Arrays may be numpy arrays (host) or torch tensors (host or CUDA); the memory
+space is passed to the library as ``HSG_HOST`` / ``HSG_DEVICE``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhsg.so")
+
+HSG_OK, HSG_EINVAL, HSG_ENOMEM, HSG_ECUDA, HSG_ETIMEOUT, HSG_EBUSY = range(6)
+HSG_NONE, HSG_METROPOLIS, HSG_HEATBATH, HSG_OVERRELAX = range(4)
+HSG_PROP_SPHERE, HSG_PROP_BALL = 0, 1
+HSG_F32, HSG_F64 = 0, 1
+HSG_HOST, HSG_DEVICE = 0, 1
+HSG_KERNEL_AUTO, HSG_KERNEL_GLOBAL, HSG_KERNEL_SLAB = 0, 1, 2
+(HSG_PROF_INIT, HSG_PROF_LAYOUT, HSG_PROF_OVERRELAX, HSG_PROF_METROPOLIS, HSG_PROF_HEATBATH,
+ HSG_PROF_ENERGY, HSG_PROF_RENORM, HSG_PROF_COUNT) = range(8)
+
+
+class HsgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class hsg_schedule(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int),
+        ("hits", ctypes.c_int),
+        ("proposal", ctypes.c_int),
+        ("step", ctypes.c_float),
+        ("n_or", ctypes.c_int),
+        ("T", ctypes.c_double),
+        ("renorm_every", ctypes.c_int),
+        ("energy_every", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+    ]
+
+
+def schedule(kind=HSG_NONE, hits=1, proposal=HSG_PROP_SPHERE, step=0.5, n_or=0, T=1.0, renorm_every=0,
+             energy_every=0, kernel=HSG_KERNEL_AUTO) -> hsg_schedule:
+    """A filled ``hsg_schedule`` (T may be ``math.inf``)."""
+    return hsg_schedule(int(kind), int(hits), int(proposal), float(step), int(n_or), float(T), int(renorm_every),
+                        int(energy_every), int(kernel))
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+_vp, _i, _u32, _u64, _d = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_double
+_sch_p = ctypes.POINTER(hsg_schedule)
+
+_SIGS = {
+    "hsg_create": ([ctypes.POINTER(_vp), _i, _u64, _u32, _u32, _vp], _i),
+    "hsg_destroy": ([_vp], _i),
+    "hsg_set_couplings": ([_vp, _vp, _i, _i], _i),
+    "hsg_sweep": ([_vp, _sch_p, _i], _i),
+    "hsg_energy": ([_vp, ctypes.POINTER(_d)], _i),
+    "hsg_get_energy_log": ([_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)], _i),
+    "hsg_clear_energy_log": ([_vp], _i),
+    "hsg_get_spins": ([_vp, _vp, _i], _i),
+    "hsg_set_spins": ([_vp, _vp, _i], _i),
+    "hsg_get_sweep": ([_vp, ctypes.POINTER(_u64)], _i),
+    "hsg_set_sweep": ([_vp, _u64], _i),
+    "hsg_half_sweep": ([_vp, _sch_p, _i, _i], _i),
+    "hsg_renorm": ([_vp], _i),
+    "hsg_profile": ([_vp, _i], _i),
+    "hsg_profile_read": ([_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_u64)], _i),
+    "hsg_profile_reset": ([_vp], _i),
+    "hsg_launch_count": ([_vp, ctypes.POINTER(_u64)], _i),
+    "hsg_last_error": ([_vp], ctypes.c_char_p),
+    "hsg_status_string": ([_i], ctypes.c_char_p),
+    "hsg_version": ([], _i),
+    "hsg_philox": ([_u64, _u32, _u32, _u32, _u32, _u32, _u32, _vp, _vp], _i),
+    "hsg_test_fail_alloc": ([_i], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+def _status_name(s: int) -> str:
+    return _lib.hsg_status_string(int(s)).decode()
+
+
+def _check(status: int, ctx=None) -> None:
+    if status != HSG_OK:
+        msg = _lib.hsg_last_error(ctx).decode()
+        raise HsgError(status, msg)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _array_ptr(a, want_dtype=None):
+    """(pointer, where, dtype code, n elements) of a numpy array or torch tensor."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        code = {torch.float32: HSG_F32, torch.float64: HSG_F64}.get(a.dtype)
+        where = HSG_DEVICE if a.is_cuda else HSG_HOST
+        return a.data_ptr(), where, code, a.numel()
+    a = np.asarray(a)
+    if not a.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    code = {np.dtype(np.float32): HSG_F32, np.dtype(np.float64): HSG_F64}.get(a.dtype)
+    return a.ctypes.data, HSG_HOST, code, a.size
+
+
+# ---------------------------------------------------------------------------
+# C names
+# ---------------------------------------------------------------------------
+
+def hsg_create(L: int, seed: int, sample: int = 0, replica: int = 0, stream=None) -> ctypes.c_void_p:
+    ctx = _vp()
+    _check(_lib.hsg_create(ctypes.byref(ctx), int(L), int(seed), int(sample), int(replica), _stream_ptr(stream)))
+    return ctx
+
+
+def hsg_destroy(ctx) -> None:
+    _check(_lib.hsg_destroy(ctx))
+
+
+def hsg_set_couplings(ctx, J) -> None:
+    ptr, where, code, n = _array_ptr(J)
+    if code is None:
+        raise TypeError("couplings must be float32 or float64")
+    _check(_lib.hsg_set_couplings(ctx, ptr, code, where), ctx)
+
+
+def hsg_sweep(ctx, sched: hsg_schedule, n_sweeps: int) -> None:
+    _check(_lib.hsg_sweep(ctx, ctypes.byref(sched), int(n_sweeps)), ctx)
+
+
+def hsg_energy(ctx) -> float:
+    e = _d(0.0)
+    _check(_lib.hsg_energy(ctx, ctypes.byref(e)), ctx)
+    return e.value
+
+
+def hsg_get_energy_log(ctx) -> np.ndarray:
+    n = _i(0)
+    _check(_lib.hsg_get_energy_log(ctx, None, 0, ctypes.byref(n)), ctx)
+    out = np.zeros(n.value, dtype=np.float64)
+    if n.value:
+        _check(_lib.hsg_get_energy_log(ctx, out.ctypes.data_as(ctypes.POINTER(_d)), n.value, ctypes.byref(n)), ctx)
+    return out
+
+
+def hsg_clear_energy_log(ctx) -> None:
+    _check(_lib.hsg_clear_energy_log(ctx), ctx)
+
+
+def hsg_get_spins(ctx, out) -> None:
+    ptr, where, code, _ = _array_ptr(out)
+    if code != HSG_F32:
+        raise TypeError("spins are float32")
+    _check(_lib.hsg_get_spins(ctx, ptr, where), ctx)
+
+
+def hsg_set_spins(ctx, spins) -> None:
+    ptr, where, code, _ = _array_ptr(spins)
+    if code != HSG_F32:
+        raise TypeError("spins are float32")
+    _check(_lib.hsg_set_spins(ctx, ptr, where), ctx)
+
+
+def hsg_get_sweep(ctx) -> int:
+    v = _u64(0)
+    _check(_lib.hsg_get_sweep(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def hsg_set_sweep(ctx, sweep: int) -> None:
+    _check(_lib.hsg_set_sweep(ctx, int(sweep)), ctx)
+
+
+def hsg_half_sweep(ctx, sched: hsg_schedule, update: int, colour: int) -> None:
+    _check(_lib.hsg_half_sweep(ctx, ctypes.byref(sched), int(update), int(colour)), ctx)
+
+
+def hsg_renorm(ctx) -> None:
+    _check(_lib.hsg_renorm(ctx), ctx)
+
+
+def hsg_profile(ctx, on: bool) -> None:
+    _check(_lib.hsg_profile(ctx, 1 if on else 0), ctx)
+
+
+def hsg_profile_read(ctx, kclass: int):
+    ms, n = _d(0.0), _u64(0)
+    _check(_lib.hsg_profile_read(ctx, int(kclass), ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def hsg_profile_reset(ctx) -> None:
+    _check(_lib.hsg_profile_reset(ctx), ctx)
+
+
+def hsg_launch_count(ctx) -> int:
+    v = _u64(0)
+    _check(_lib.hsg_launch_count(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
+def hsg_last_error(ctx=None) -> str:
+    return _lib.hsg_last_error(ctx).decode()
+
+
+def hsg_status_string(status: int) -> str:
+    return _status_name(status)
+
+
+def hsg_version() -> int:
+    return _lib.hsg_version()
+
+
+def hsg_philox(seed: int, sample: int, replica: int, c1: int, c2: int, c3: int, out, stream=None) -> None:
+    ptr, where, _, n = _array_ptr(out)
+    if where != HSG_DEVICE:
+        raise ValueError("out must be a CUDA tensor of 4*n uint32 (int32) words")
+    _check(_lib.hsg_philox(int(seed), int(sample), int(replica), int(c1), int(c2), int(c3), n // 4, ptr,
+                           _stream_ptr(stream)))
+
+
+def hsg_test_fail_alloc(k: int) -> None:
+    _check(_lib.hsg_test_fail_alloc(int(k)))
+
+
+# ---------------------------------------------------------------------------
+# Convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Lattice:
+    """One L^3 lattice on the current CUDA device (a thin wrapper over a context)."""
+
+    def __init__(self, L: int, seed: int, sample: int = 0, replica: int = 0, stream=None):
+        self.L = int(L)
+        self.N = self.L ** 3
+        self.ctx = hsg_create(L, seed, sample, replica, stream)
+
+    def close(self) -> None:
+        if self.ctx is not None and self.ctx.value:
+            hsg_destroy(self.ctx)
+        self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_couplings(self, J) -> None:
+        hsg_set_couplings(self.ctx, J)
+
+    def sweep(self, sched: hsg_schedule, n_sweeps: int = 1) -> None:
+        hsg_sweep(self.ctx, sched, n_sweeps)
+
+    def half_sweep(self, sched: hsg_schedule, update: int, colour: int) -> None:
+        hsg_half_sweep(self.ctx, sched, update, colour)
+
+    def energy(self) -> float:
+        return hsg_energy(self.ctx)
+
+    def energy_log(self) -> np.ndarray:
+        return hsg_get_energy_log(self.ctx)
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros(3 * self.N, dtype=np.float32)
+        hsg_get_spins(self.ctx, out)
+        return out
+
+    def set_spins(self, s) -> None:
+        hsg_set_spins(self.ctx, s)
+
+    def renorm(self) -> None:
+        hsg_renorm(self.ctx)
+
+    @property
+    def sweep_count(self) -> int:
+        return hsg_get_sweep(self.ctx)
+
+    @sweep_count.setter
+    def sweep_count(self, v: int) -> None:
+        hsg_set_sweep(self.ctx, v)

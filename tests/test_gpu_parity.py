@@ -1,0 +1,393 @@
+"""GPU path vs the FP64 oracle, through the C ABI (needs a CUDA GPU).
+
+Tolerances (written per test):
+  * over-relaxation half-sweeps: max |diff| <= 1e-5 per spin component;
+  * Metropolis half-sweeps: spins agree to 1e-5 at every site whose
+    accept decisions all lie farther than 1e-5 from their threshold
+    (|u3 - exp(-beta dE)| >= 1e-5, margin reported by the oracle);
+  * heat-bath half-sweeps: 1e-5 at every site whose field is not within
+    1e-5 (relative) of the h_z = 0 plane, where the orthonormal frame of
+    the azimuth switches branch and fp32/fp64 may pick different branches;
+  * energies: |E/N difference| <= 2e-6 (per-site fields are fp32);
+  * long runs: mean E/N within 3 sigma (binned errors of both runs).
+Every half-sweep starts the GPU and the oracle from the same state (fp32
+values, the oracle holding them in fp64) and the same fp32-rounded J.
+"""
+import ctypes
+import math
+import os
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1006_2566_gb300 import inputs  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def hsg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1006_2566_gb300 import build
+
+    build.build()
+    oracle.build()
+    from paper_1006_2566_gb300 import hsg as h
+
+    return h
+
+
+VARIANTS = [1, 2]  # HSG_KERNEL_GLOBAL, HSG_KERNEL_SLAB
+
+
+def gpu_half_sweep(hsg, L, J, s32, update, colour, sched, seed=7, sample=0, replica=0, sweep=0):
+    with hsg.Lattice(L, seed, sample, replica) as lat:
+        lat.set_couplings(J)
+        lat.set_spins(s32)
+        lat.sweep_count = sweep
+        lat.half_sweep(sched, update, colour)
+        return lat.spins().astype(np.float64)
+
+
+def oracle_state(L, seed_j, seed_s):
+    J = inputs.gaussian_couplings(L, seed=seed_j)
+    s32 = inputs.random_spins(L, seed=seed_s, dtype=np.float32)
+    return J, s32
+
+
+def colour_mask(L, c):
+    g = np.indices((L, L, L))
+    return (((g[0] + g[1] + g[2]) % 2) == c).reshape(-1)
+
+
+# ---------------------------------------------------------------------------
+# Philox
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def curand_lib():
+    d = tempfile.mkdtemp(prefix="hsg_curand_")
+    so = os.path.join(d, "curand_philox.so")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", "-Xcompiler", "-fPIC", "-shared",
+                    "-o", so, os.path.join(ROOT, "tests", "native", "curand_philox.cu")], check=True)
+    lib = ctypes.CDLL(so)
+    lib.curand_philox_fill.argtypes = [ctypes.c_uint32] * 6 + [ctypes.c_void_p]
+    lib.curand_philox_fill.restype = ctypes.c_int
+    return lib
+
+
+@pytest.mark.parametrize("seed,sample,replica,c1,c2,c3", [
+    (1, 0, 0, 0, (1 << 24), 0),
+    (0xDEADBEEF12345678, 3, 1, 77, (3 << 24) | (1 << 16) | 5, 9),
+])
+def test_philox_device_matches_curand_and_oracle(hsg, curand_lib, seed, sample, replica, c1, c2, c3):
+    n = 1 << 20
+    mine = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+    ref = torch.zeros(4 * n, dtype=torch.int32, device="cuda")
+    hsg.hsg_philox(seed, sample, replica, c1, c2, c3, mine)
+    k = oracle.key(seed, sample, replica)
+    assert curand_lib.curand_philox_fill(k[0], k[1], c1, c2, c3, n, ref.data_ptr()) == 0
+    torch.cuda.synchronize()
+    a = mine.cpu().numpy().view(np.uint32).reshape(n, 4)
+    b = ref.cpu().numpy().view(np.uint32).reshape(n, 4)
+    assert np.array_equal(a, b)  # all 2^20 counters, bit for bit
+    rng = np.random.default_rng(1)
+    for t in list(range(64)) + list(rng.integers(0, n, 2000)) + [n - 1]:
+        assert list(oracle.philox4x32_10((int(t), c1, c2, c3), k)) == list(b[t])
+
+
+# ---------------------------------------------------------------------------
+# Initial state and layout
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,seed,sample,replica", [(4, 1, 0, 0), (16, 1, 0, 0), (24, 9, 5, 1), (66, 3, 0, 1)])
+def test_initial_spins_match_oracle(hsg, L, seed, sample, replica):
+    with hsg.Lattice(L, seed, sample, replica) as lat:
+        got = lat.spins().astype(np.float64)
+    ref = oracle.init_spins(L, seed, sample, replica)
+    assert np.max(np.abs(got - ref)) < 1e-6
+
+
+@pytest.mark.parametrize("L", [4, 6, 40])
+def test_spin_layout_round_trip_is_exact(hsg, L):
+    s = inputs.random_spins(L, seed=5, dtype=np.float32)
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_spins(s)
+        assert np.array_equal(lat.spins(), s)
+        dev = torch.from_numpy(s).cuda()
+        lat.set_spins(dev)
+        out = torch.zeros_like(dev)
+        hsg.hsg_get_spins(lat.ctx, out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, dev)
+
+
+# ---------------------------------------------------------------------------
+# Half-sweeps
+# ---------------------------------------------------------------------------
+
+OR_SIZES = [4, 6, 8, 16, 24, 40, 66]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L", OR_SIZES)
+def test_over_relaxation_half_sweep_parity(hsg, variant, L):
+    J, s32 = oracle_state(L, 100 + L, 200 + L)
+    Jr = inputs.round_to_f32(J)
+    sched = hsg.schedule(kernel=variant)
+    for colour in (0, 1):
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_OVERRELAX, colour, sched)
+        ref = s32.astype(np.float64)
+        oracle.half_sweep(L, Jr, ref, oracle.OR, colour, oracle.Params())
+        assert np.max(np.abs(got - ref)) <= TOL
+        other = ~colour_mask(L, colour)
+        assert np.array_equal(got.reshape(-1, 3)[other], s32.astype(np.float64).reshape(-1, 3)[other])
+
+
+MET_CASES = [
+    # (L, proposal, hits, T)
+    (6, 0, 1, 1.0),
+    (16, 0, 1, 1.0),
+    (16, 1, 4, 0.5),
+    (40, 1, 4, 0.5),
+    (66, 0, 3, 0.3),
+    (24, 1, 2, math.inf),
+]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("case", MET_CASES)
+def test_metropolis_half_sweep_parity(hsg, variant, case):
+    L, proposal, hits, T = case
+    J, s32 = oracle_state(L, 300 + L, 400 + L)
+    Jr = inputs.round_to_f32(J)
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=hits, proposal=proposal, step=0.5, T=T, kernel=variant)
+    beta = 0.0 if math.isinf(T) else 1.0 / T
+    for colour in (0, 1):
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_METROPOLIS, colour, sched, seed=11, sweep=3)
+        ref = s32.astype(np.float64)
+        p = oracle.Params(key=oracle.key(11), sweep=3, beta=beta, step=0.5, hits=hits, proposal=proposal)
+        margins = oracle.half_sweep(L, Jr, ref, oracle.MET, colour, p, want_margins=True)
+        mask = colour_mask(L, colour)
+        clear = margins >= TOL
+        near = mask & ~clear
+        assert near.sum() <= max(2, 0.002 * mask.sum())
+        diff = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
+        assert np.max(diff[clear]) <= TOL
+        moved = np.any(ref.reshape(-1, 3) != s32.astype(np.float64).reshape(-1, 3), axis=1)
+        assert moved[mask].mean() > 0.05  # the chain does move
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("L,T", [(6, 1.0), (16, 0.3), (40, 0.3), (66, 1.0), (16, math.inf)])
+def test_heatbath_half_sweep_parity(hsg, variant, L, T):
+    J, s32 = oracle_state(L, 500 + L, 600 + L)
+    Jr = inputs.round_to_f32(J)
+    sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=T, kernel=variant)
+    beta = 0.0 if math.isinf(T) else 1.0 / T
+    for colour in (0, 1):
+        s64 = s32.astype(np.float64)
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_HEATBATH, colour, sched, seed=13, sample=2, sweep=5)
+        ref = s64.copy()
+        p = oracle.Params(key=oracle.key(13, 2), sweep=5, beta=beta)
+        oracle.half_sweep(L, Jr, ref, oracle.HB, colour, p)
+        mask = colour_mask(L, colour)
+        keep = mask.copy()
+        for i in np.nonzero(mask)[0]:
+            h = oracle.local_field(L, Jr, s64, int(i))
+            if abs(h[2]) < TOL * np.linalg.norm(h):
+                keep[i] = False
+        assert mask.sum() - keep.sum() <= max(2, 0.001 * mask.sum())
+        diff = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
+        assert np.max(diff[keep]) <= TOL
+        assert np.max(np.abs(np.linalg.norm(got.reshape(-1, 3)[mask], axis=1) - 1)) < 1e-5
+
+
+@pytest.mark.parametrize("L", [8, 40])
+def test_kernel_variants_are_bit_identical(hsg, L):
+    J = inputs.gaussian_couplings(L, seed=3)
+    out = []
+    for variant in VARIANTS:
+        with hsg.Lattice(L, 3) as lat:
+            lat.set_couplings(J)
+            lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, T=0.5, n_or=2, kernel=variant), 3)
+            lat.sweep(hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=2, proposal=1, T=0.5, n_or=1, kernel=variant), 2)
+            out.append(lat.spins())
+    assert np.array_equal(out[0], out[1])
+
+
+# ---------------------------------------------------------------------------
+# Energy and renormalisation
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L", [4, 6, 16, 40, 66])
+def test_energy_matches_oracle(hsg, L):
+    J, s32 = oracle_state(L, 700 + L, 800 + L)
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_couplings(J)
+        lat.set_spins(s32)
+        e = lat.energy()
+    ref = oracle.energy(L, inputs.round_to_f32(J), s32.astype(np.float64)) / L ** 3
+    assert abs(e - ref) <= 2e-6
+
+
+def test_energy_closed_forms(hsg):
+    L = 6
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_couplings(inputs.uniform_couplings(L))
+        lat.set_spins(inputs.aligned_spins(L, (0.0, 0.6, 0.8), dtype=np.float32))
+        assert abs(lat.energy() + 3.0) < 1e-6
+        for axis in range(3):
+            ang = 2 * np.pi / L
+            s = np.zeros((L, L, L, 3))
+            coord = np.indices((L, L, L))[2 - axis]
+            s[..., 0], s[..., 1] = np.cos(ang * coord), np.sin(ang * coord)
+            lat.set_couplings(inputs.uniform_couplings(L, axes=(axis,)))
+            lat.set_spins(s.reshape(-1).astype(np.float32))
+            assert abs(lat.energy() + np.cos(ang)) < 1e-6
+
+
+def test_renorm_matches_oracle(hsg):
+    L = 16
+    rng = np.random.default_rng(4)
+    s = (inputs.random_spins(L, seed=9).reshape(-1, 3) * rng.uniform(0.5, 2.0, size=(L ** 3, 1))).reshape(-1)
+    s32 = s.astype(np.float32)
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_spins(s32)
+        lat.renorm()
+        got = lat.spins()
+    ref = s32.astype(np.float64)
+    oracle.renorm(L, ref)
+    assert np.max(np.abs(got.astype(np.float64) - ref)) <= 2 ** -24
+    assert np.max(np.abs(np.linalg.norm(got.astype(np.float64).reshape(-1, 3), axis=1) - 1)) < 2e-7
+
+
+# ---------------------------------------------------------------------------
+# Whole sweeps
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_sweep_schedule_matches_oracle(hsg, variant):
+    """hsg_sweep = main update (both colours), n_or OR sweeps, counter,
+    renormalisation, energy log: the same composition as the oracle."""
+    L = 16
+    J = inputs.gaussian_couplings(L, seed=17)
+    sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=0.8, n_or=2, renorm_every=1, energy_every=1, kernel=variant)
+    with hsg.Lattice(L, 17) as lat:
+        lat.set_couplings(J)
+        s0 = lat.spins().astype(np.float64)
+        lat.sweep(sched, 2)
+        got = lat.spins().astype(np.float64)
+        elog = lat.energy_log()
+        assert lat.sweep_count == 2
+    s = s0.copy()
+    sch = oracle.Schedule(kind=oracle.HB, beta=1 / 0.8, n_or=2, renorm_every=1, energy_every=1)
+    sw, ref_log = oracle.sweeps(L, inputs.round_to_f32(J), s, sch, oracle.key(17), 2)
+    assert sw == 2 and len(elog) == 2
+    assert np.max(np.abs(elog - ref_log)) < 1e-5
+    assert np.max(np.abs(got - s)) < 1e-4
+
+
+def test_long_run_energy_statistics_match_oracle(hsg):
+    """L = 16, Gaussian J, Metropolis 1 hit (sphere), T = 1: the mean E/N of
+    1500 sweeps agrees with the oracle's within 3 sigma."""
+    L, n = 16, 1500
+    J = inputs.gaussian_couplings(L, seed=1)
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_couplings(J)
+        lat.sweep(hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=1, T=1.0, energy_every=1), n)
+        g = lat.energy_log()
+    s = oracle.init_spins(L, 1)
+    _, r = oracle.sweeps(L, inputs.round_to_f32(J), s, oracle.Schedule(kind=oracle.MET, beta=1.0, energy_every=1),
+                         oracle.key(1), n)
+
+    def binned(x):
+        b = np.array([v.mean() for v in np.array_split(x[n // 5:], 20)])
+        return b.mean(), b.std(ddof=1) / np.sqrt(len(b))
+
+    mg, eg = binned(g)
+    mr, er = binned(r)
+    assert abs(mg - mr) < 3 * math.hypot(eg, er) + 1e-6, (mg, eg, mr, er)
+
+
+def test_checkpoint_resume_is_bit_identical(hsg):
+    L = 24
+    J = inputs.gaussian_couplings(L, seed=5)
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=2, proposal=1, T=0.7, n_or=1, renorm_every=2)
+    with hsg.Lattice(L, 5) as a:
+        a.set_couplings(J)
+        a.sweep(sched, 6)
+        want = a.spins()
+    with hsg.Lattice(L, 5) as b:
+        b.set_couplings(J)
+        b.sweep(sched, 3)
+        mid, sw = b.spins(), b.sweep_count
+    with hsg.Lattice(L, 5) as c:
+        c.set_couplings(J)
+        c.set_spins(mid)
+        c.sweep_count = sw
+        c.sweep(sched, 3)
+        assert np.array_equal(c.spins(), want)
+
+
+# ---------------------------------------------------------------------------
+# Boundary behaviour on a device
+# ---------------------------------------------------------------------------
+
+def test_error_paths_on_device(hsg):
+    with hsg.Lattice(8, 1) as lat:
+        with pytest.raises(hsg.HsgError) as e:
+            lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH), 1)
+        assert e.value.status == hsg.HSG_EINVAL and "couplings" in str(e.value)
+        lat.set_couplings(inputs.gaussian_couplings(8, seed=1))
+        bad = [dict(kind=7), dict(hits=0), dict(hits=70000), dict(proposal=3), dict(step=0.0), dict(n_or=-1),
+               dict(T=0.0), dict(T=-1.0), dict(T=float("nan")), dict(renorm_every=-1), dict(kernel=9)]
+        for kw in bad:
+            with pytest.raises(hsg.HsgError) as e:
+                lat.sweep(hsg.schedule(**kw), 1)
+            assert e.value.status == hsg.HSG_EINVAL, kw
+        with pytest.raises(hsg.HsgError):
+            lat.sweep(hsg.schedule(), -1)
+        lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH), 0)  # no-op
+        assert lat.sweep_count == 0
+        with pytest.raises(hsg.HsgError):
+            lat.half_sweep(hsg.schedule(), hsg.HSG_OVERRELAX, 2)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5])
+def test_injected_allocation_failure_is_reported(hsg, k):
+    hsg.hsg_test_fail_alloc(k)
+    try:
+        with pytest.raises(hsg.HsgError) as e:
+            hsg.hsg_create(16, seed=1)
+        assert e.value.status == hsg.HSG_ENOMEM
+    finally:
+        hsg.hsg_test_fail_alloc(0)
+    with hsg.Lattice(16, 1) as lat:  # the library is still usable
+        lat.set_couplings(inputs.gaussian_couplings(16, seed=1))
+        lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH), 1)
+
+
+def test_profiler_counts_launches(hsg):
+    with hsg.Lattice(16, 1) as lat:
+        lat.set_couplings(inputs.gaussian_couplings(16, seed=1))
+        n0 = hsg.hsg_launch_count(lat.ctx)
+        hsg.hsg_profile(lat.ctx, True)
+        lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, n_or=4, energy_every=5, renorm_every=5), 10)
+        counts = {k: hsg.hsg_profile_read(lat.ctx, k)[1] for k in range(hsg.HSG_PROF_COUNT)}
+        ms = hsg.hsg_profile_read(lat.ctx, hsg.HSG_PROF_OVERRELAX)[0]
+        assert counts[hsg.HSG_PROF_HEATBATH] == 20
+        assert counts[hsg.HSG_PROF_OVERRELAX] == 80
+        assert counts[hsg.HSG_PROF_ENERGY] == 2 and counts[hsg.HSG_PROF_RENORM] == 2
+        assert ms > 0
+        assert hsg.hsg_launch_count(lat.ctx) - n0 == 20 + 80 + 2 * 2 + 2
+        hsg.hsg_profile_reset(lat.ctx)
+        assert hsg.hsg_profile_read(lat.ctx, hsg.HSG_PROF_OVERRELAX)[1] == 0
