@@ -85,10 +85,9 @@ def parse_args():
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    from paper_1006_2566_gb300 import dist as hdist
+
+    return hdist.env()
 
 
 # ---------------------------------------------------------------------------
@@ -227,6 +226,7 @@ def run_ours(args, wl):
         build.build()
     if world > 1:
         torch.distributed.barrier()
+    from paper_1006_2566_gb300 import dist as hdist
     from paper_1006_2566_gb300 import hsg, inputs
 
     L = wl["L"]
@@ -238,7 +238,7 @@ def run_ours(args, wl):
                          renorm_every=wl["renorm_every"], energy_every=wl["energy_every"], kernel=kernel)
     sps = wl["sweeps_per_step"]
     stream = torch.cuda.Stream()
-    sample = rank  # weak scaling: one disorder sample per rank
+    sample = hdist.rank_sample(rank)  # weak scaling: one disorder sample per rank
     J = inputs.gaussian_couplings(L, seed=wl["seed"], sample=sample, dtype=np.float32)
     lat = hsg.Lattice(L, wl["seed"], sample, 0, stream)
     lat.set_couplings(J)
@@ -269,10 +269,7 @@ def run_ours(args, wl):
     per_class = {k: hsg.hsg_profile_read(lat.ctx, k) for k in range(hsg.HSG_PROF_COUNT)}
     hsg.hsg_profile(lat.ctx, False)
     e_last = float(lat.energy_log()[-1]) if wl["energy_every"] else float("nan")
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = hdist.max_over_ranks(elapsed_ms, device="cuda")
 
     # ---- end to end through the C ABI, from pinned host memory -------------
     e2e = None
@@ -300,10 +297,7 @@ def run_ours(args, wl):
             hsg.hsg_get_spins(lat.ctx, s_out)  # D2H 12N bytes, synchronises
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - w0) * 1e3
-        if world > 1:
-            t = torch.tensor([e2e_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = hdist.max_over_ranks(e2e_ms, device="cuda")
         e2e = {"value": round(world * step_units(wl) * args.steps / (e2e_ms * 1e6), 4), "unit": "spin updates/ns",
                "h2d_bytes_per_step": int(Jh.numel() * 4 + s_in.numel() * 4),
                "d2h_bytes_per_step": int(8 + s_out.numel() * 4), "ms_per_step": round(e2e_ms / args.steps, 4)}
@@ -315,8 +309,7 @@ def run_ours(args, wl):
             torch.distributed.destroy_process_group()
         return
 
-    units = step_units(wl) * args.steps * world
-    value = units / (elapsed_ms * 1e6)
+    value = hdist.job_throughput(step_units(wl) * args.steps, world, elapsed_ms * 1e6)
     peak, peak_kind = measured_peaks()
     or_ms, or_n = per_class[hsg.HSG_PROF_OVERRELAX]
     hb_ms, hb_n = per_class[hsg.HSG_PROF_HEATBATH]

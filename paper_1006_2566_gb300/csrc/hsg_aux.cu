@@ -80,8 +80,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // Energy, first pass.  Every bond joins a colour-0 and a colour-1 site, so
 // sum_bonds J s_i.s_j = sum over colour-0 sites of s_i . h_i with h_i the
-// local field of Eq. 2.  h is formed in FP32 (as in the updates); the dot
-// product and every sum are FP64.  Block b writes partials[b].
+// local field of Eq. 2.  The site term s_i . h_i is formed in FP32 (as in
+// the updates, relative error a few ulp); every sum over sites is FP64.
+// Block b writes partials[b].
 __global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const float4* __restrict__ S,
                                                                    const float* __restrict__ J, int L,
                                                                    double* __restrict__ partials) {
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const float4*
                                  __ldg(s1 + q_zp), __ldg(s1 + q_zm), __ldg(jx0 + t), __ldg(jx1 + q_xm),
                                  __ldg(jy0 + t), __ldg(jy1 + q_ym), __ldg(jz0 + t), __ldg(jz1 + q_zm));
     const float4 s = __ldg(s0 + t);
-    acc = fma((double)s.x, (double)h.x, fma((double)s.y, (double)h.y, fma((double)s.z, (double)h.z, acc)));
+    acc += (double)dot3(make_float3(s.x, s.y, s.z), h);
   }
   __shared__ double warp_part[ENERGY_THREADS / 32];
   acc = warp_sum(acc);
@@ -138,20 +139,32 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_energy_final(const double* __
   }
 }
 
-// Renormalisation s <- s/|s|: |s|^2 from the exact fp64 squares of the
-// fp32 components, the reciprocal square root in fp64, the result rounded
-// once to fp32.
+// Renormalisation s <- s/|s|.  d = |s|^2 - 1 is formed in fp64 from the
+// exact squares of the fp32 components (three FMAs, error ~1e-16).  Spins
+// drift from unit length only by fp32 round-off, so |d| is tiny and
+// 1/sqrt(1+d) - 1 = -d/2 + 3d^2/8 - 5d^3/16 + O(d^4) (binomial series; for
+// |d| < 2^-8 the remainder is below 2^-33) is evaluated in fp32 and applied
+// as s + s*c with one rounding: the result is within a hair of the
+// correctly rounded s/|s|.  Larger |d| takes the fp64 reciprocal square
+// root; a zero spin is left as is.
 __global__ void k_renorm(float4* __restrict__ S, long long n) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     float4 v = S[t];
-    const double n2 = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, (double)v.z * (double)v.z));
-    if (n2 > 0.0) {
-      const double r = rsqrt(n2);
-      v.x = (float)(v.x * r);
-      v.y = (float)(v.y * r);
-      v.z = (float)(v.z * r);
-      S[t] = v;
+    const double dx = v.x, dy = v.y, dz = v.z;
+    const double d = fma(dx, dx, fma(dy, dy, fma(dz, dz, -1.0)));
+    const float df = (float)d;
+    if (fabsf(df) < 0x1p-8f) {
+      const float c = df * fmaf(df, fmaf(df, -0.3125f, 0.375f), -0.5f);
+      v.x = fmaf(v.x, c, v.x);
+      v.y = fmaf(v.y, c, v.y);
+      v.z = fmaf(v.z, c, v.z);
+    } else if (d > -1.0) {
+      const double r = rsqrt(d + 1.0);
+      v.x = (float)(dx * r);
+      v.y = (float)(dy * r);
+      v.z = (float)(dz * r);
     }
+    S[t] = v;
   }
 }
 

@@ -97,10 +97,16 @@ __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t
 }
 
 // Heat-bath: s' from the density prop. to exp(beta s'.h) on S^2.  With
-// x = beta|h|, 1 - cos(theta) = -log1p(u0 expm1(-2x))/x inverts the CDF of
-// cos(theta); the azimuth 2 pi u1 is taken in the orthonormal frame of
-// h/|h| built as in Duff et al., "Building an Orthonormal Basis,
+// x = beta|h|, 1 - cos(theta) = -log(1 + v)/x, v = u0 expm1(-2x), inverts
+// the CDF of cos(theta); the azimuth 2 pi u1 is taken in the orthonormal
+// frame of h/|h| built as in Duff et al., "Building an Orthonormal Basis,
 // Revisited" (JCGT 2017).  Uniform on S^2 when x < 1e-6.
+//
+// fp32 evaluation of log(1 + v): log1p(v) where 1 + v >= 1/2; below that
+// 1 + v = (1 - u0) + u0 e^{-2x} is summed from two positive terms (1 - u0
+// is exact), since forming 1 + v directly cancels when u0 (1 - e^{-2x})
+// is close to 1.  q = 1 - e^{-2x} comes from expm1 for small x and from
+// 1 - e^{-2x} (error <= 1 ulp of q) once e^{-2x} <= 1/2.
 __device__ __forceinline__ float3 update_heatbath(float3 h, uint32_t site, uint32_t colour, uint32_t sweep_lo,
                                                   uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta) {
   const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_HB << 24) | (colour << 16), sweep_hi), k0, k1);
@@ -110,7 +116,11 @@ __device__ __forceinline__ float3 update_heatbath(float3 h, uint32_t site, uint3
   if (!(x >= 1e-6f)) return sphere_point(u0, u1);
   const float inv = 1.0f / hn;
   const float3 n = make_float3(h.x * inv, h.y * inv, h.z * inv);
-  float sv = -log1pf(u0 * expm1f(-2.0f * x)) / x;
+  const float e2x = expf(-2.0f * x);
+  const float q = e2x > 0.5f ? -expm1f(-2.0f * x) : 1.0f - e2x;
+  const float v = -u0 * q;
+  const float lg = v > -0.5f ? log1pf(v) : logf(fmaf(u0, e2x, 1.0f - u0));
+  float sv = -lg / x;
   sv = fminf(fmaxf(sv, 0.0f), 2.0f);
   const float ct = 1.0f - sv;
   const float st = sqrtf(fmaxf(sv * (2.0f - sv), 0.0f));

@@ -1,14 +1,19 @@
 """GPU path vs the FP64 oracle, through the C ABI (needs a CUDA GPU).
 
 Tolerances (written per test):
-  * over-relaxation half-sweeps: max |diff| <= 1e-5 per spin component;
-  * Metropolis half-sweeps: spins agree to 1e-5 at every site whose
-    accept decisions all lie farther than 1e-5 from their threshold
-    (|u3 - exp(-beta dE)| >= 1e-5, margin reported by the oracle);
-  * heat-bath half-sweeps: 1e-5 at every site whose field is not within
-    1e-5 (relative) of the h_z = 0 plane, where the orthonormal frame of
-    the azimuth switches branch and fp32/fp64 may pick different branches;
-  * energies: |E/N difference| <= 2e-6 (per-site fields are fp32);
+  * half-sweeps: max |diff| <= 1e-5 per spin component at every site whose
+    fp32 local field is well conditioned, 4 kappa <= 1e-5 with
+    kappa = 2^-24 * sum_k |J_k| / |h| (the field's fp32 round-off relative
+    to its length, which the update's direction inherits).  At the rare
+    sites with a nearly cancelling field (<= 0.1 %) the difference must
+    stay within 1e-5 + 64 kappa, the propagated round-off bound;
+  * Metropolis: sites whose accept decisions lie within 1e-5 of their
+    threshold (|u3 - exp(-beta dE)| < 1e-5, margin reported by the oracle)
+    are excluded: fp32 and fp64 may decide differently there;
+  * heat-bath: sites whose field is within 1e-5 (relative) of the h_z = 0
+    plane are excluded: the orthonormal frame of the azimuth switches
+    branch there and fp32/fp64 may pick different branches;
+  * energies: |E/N difference| <= 2e-6 (per-site terms are fp32);
   * long runs: mean E/N within 3 sigma (binned errors of both runs).
 Every half-sweep starts the GPU and the oracle from the same state (fp32
 values, the oracle holding them in fp64) and the same fp32-rounded J.
@@ -63,9 +68,47 @@ def oracle_state(L, seed_j, seed_s):
     return J, s32
 
 
+U32 = 2.0 ** -24
+
+
 def colour_mask(L, c):
     g = np.indices((L, L, L))
     return (((g[0] + g[1] + g[2]) % 2) == c).reshape(-1)
+
+
+def bond_sums(L, J):
+    """sum of |J| over the six bonds of every site."""
+    a = np.abs(J.reshape(L, L, L, 3))  # [z, y, x, d]
+    s = a.sum(axis=3)
+    s += np.roll(a[..., 0], 1, axis=2) + np.roll(a[..., 1], 1, axis=1) + np.roll(a[..., 2], 1, axis=0)
+    return s.reshape(-1)
+
+
+def check_half_sweep(L, Jr, before64, got, ref, colour, exclude=None):
+    """Compare one half-sweep site by site (see the module docstring).
+    Returns (number of ill-conditioned sites, max err/kappa)."""
+    idx = np.nonzero(colour_mask(L, colour))[0]
+    h = np.array([oracle.local_field(L, Jr, before64, int(i)) for i in idx])
+    hn = np.linalg.norm(h, axis=1)
+    kappa = U32 * bond_sums(L, Jr)[idx] / np.maximum(hn, 1e-300)
+    err = np.max(np.abs(got - ref).reshape(-1, 3)[idx], axis=1)
+    skip = np.zeros(len(idx), bool) if exclude is None else exclude[idx]
+    well = (4 * kappa <= TOL) & ~skip
+    ill = ~well & ~skip
+    assert np.all(err[well] <= TOL), float(np.max(err[well]))
+    assert ill.sum() <= max(2, 0.001 * len(idx)), int(ill.sum())
+    assert np.all(err[ill] <= TOL + 64 * kappa[ill])
+    keep = ~skip
+    return int(ill.sum()), float(np.max(err[keep] / kappa[keep])) if keep.any() else 0.0
+
+
+def frame_band(L, Jr, before64, colour):
+    """Sites whose field lies within 1e-5 (relative) of the h_z = 0 plane."""
+    band = np.zeros(L ** 3, bool)
+    for i in np.nonzero(colour_mask(L, colour))[0]:
+        h = oracle.local_field(L, Jr, before64, int(i))
+        band[i] = abs(h[2]) < TOL * np.linalg.norm(h)
+    return band
 
 
 # ---------------------------------------------------------------------------
@@ -145,9 +188,10 @@ def test_over_relaxation_half_sweep_parity(hsg, variant, L):
     sched = hsg.schedule(kernel=variant)
     for colour in (0, 1):
         got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_OVERRELAX, colour, sched)
-        ref = s32.astype(np.float64)
+        before = s32.astype(np.float64)
+        ref = before.copy()
         oracle.half_sweep(L, Jr, ref, oracle.OR, colour, oracle.Params())
-        assert np.max(np.abs(got - ref)) <= TOL
+        check_half_sweep(L, Jr, before, got, ref, colour)
         other = ~colour_mask(L, colour)
         assert np.array_equal(got.reshape(-1, 3)[other], s32.astype(np.float64).reshape(-1, 3)[other])
 
@@ -173,15 +217,14 @@ def test_metropolis_half_sweep_parity(hsg, variant, case):
     beta = 0.0 if math.isinf(T) else 1.0 / T
     for colour in (0, 1):
         got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_METROPOLIS, colour, sched, seed=11, sweep=3)
-        ref = s32.astype(np.float64)
+        before = s32.astype(np.float64)
+        ref = before.copy()
         p = oracle.Params(key=oracle.key(11), sweep=3, beta=beta, step=0.5, hits=hits, proposal=proposal)
         margins = oracle.half_sweep(L, Jr, ref, oracle.MET, colour, p, want_margins=True)
         mask = colour_mask(L, colour)
-        clear = margins >= TOL
-        near = mask & ~clear
+        near = mask & (margins < TOL)
         assert near.sum() <= max(2, 0.002 * mask.sum())
-        diff = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
-        assert np.max(diff[clear]) <= TOL
+        check_half_sweep(L, Jr, before, got, ref, colour, exclude=near)
         moved = np.any(ref.reshape(-1, 3) != s32.astype(np.float64).reshape(-1, 3), axis=1)
         assert moved[mask].mean() > 0.05  # the chain does move
 
@@ -200,14 +243,9 @@ def test_heatbath_half_sweep_parity(hsg, variant, L, T):
         p = oracle.Params(key=oracle.key(13, 2), sweep=5, beta=beta)
         oracle.half_sweep(L, Jr, ref, oracle.HB, colour, p)
         mask = colour_mask(L, colour)
-        keep = mask.copy()
-        for i in np.nonzero(mask)[0]:
-            h = oracle.local_field(L, Jr, s64, int(i))
-            if abs(h[2]) < TOL * np.linalg.norm(h):
-                keep[i] = False
-        assert mask.sum() - keep.sum() <= max(2, 0.001 * mask.sum())
-        diff = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
-        assert np.max(diff[keep]) <= TOL
+        band = frame_band(L, Jr, s64, colour)
+        assert band.sum() <= max(2, 0.001 * mask.sum())
+        check_half_sweep(L, Jr, s64, got, ref, colour, exclude=band)
         assert np.max(np.abs(np.linalg.norm(got.reshape(-1, 3)[mask], axis=1) - 1)) < 1e-5
 
 
@@ -255,10 +293,18 @@ def test_energy_closed_forms(hsg):
             assert abs(lat.energy() + np.cos(ang)) < 1e-6
 
 
-def test_renorm_matches_oracle(hsg):
+@pytest.mark.parametrize("scale", ["far", "near"])
+def test_renorm_matches_oracle(hsg, scale):
+    """Far from unit length (fp64 reciprocal square root) and within fp32
+    round-off of it (the series branch): within 1 ulp of the fp64 result."""
     L = 16
     rng = np.random.default_rng(4)
-    s = (inputs.random_spins(L, seed=9).reshape(-1, 3) * rng.uniform(0.5, 2.0, size=(L ** 3, 1))).reshape(-1)
+    if scale == "far":
+        f = rng.uniform(0.5, 2.0, size=(L ** 3, 1))
+    else:
+        f = 1.0 + rng.uniform(-3e-7, 3e-7, size=(L ** 3, 1))
+        f[:10] = 1.0 + 0.003  # just inside the series branch
+    s = (inputs.random_spins(L, seed=9).reshape(-1, 3) * f).reshape(-1)
     s32 = s.astype(np.float32)
     with hsg.Lattice(L, 1) as lat:
         lat.set_spins(s32)
@@ -275,9 +321,45 @@ def test_renorm_matches_oracle(hsg):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("kind", ["HB", "MET"])
+def test_sweep_is_the_composition_of_half_sweeps(hsg, variant, kind):
+    """hsg_sweep = main update on colour 0 then 1, n_or OR sweeps, counter
+    advance, renormalisation, energy log: bit-identical to issuing the same
+    half-sweeps one by one."""
+    L = 24
+    J = inputs.gaussian_couplings(L, seed=19)
+    k = hsg.HSG_HEATBATH if kind == "HB" else hsg.HSG_METROPOLIS
+    sched = hsg.schedule(kind=k, hits=3, proposal=1, T=0.8, n_or=2, renorm_every=2, energy_every=1, kernel=variant)
+    with hsg.Lattice(L, 19) as a:
+        a.set_couplings(J)
+        a.sweep(sched, 3)
+        want, want_log = a.spins(), a.energy_log()
+    with hsg.Lattice(L, 19) as b:
+        b.set_couplings(J)
+        got_log = []
+        for sw in range(3):
+            b.sweep_count = sw
+            for c in (0, 1):
+                b.half_sweep(sched, k, c)
+            for _ in range(2):
+                for c in (0, 1):
+                    b.half_sweep(sched, hsg.HSG_OVERRELAX, c)
+            if (sw + 1) % 2 == 0:
+                b.renorm()
+            got_log.append(b.energy())
+        assert np.array_equal(b.spins(), want)
+        assert np.array_equal(np.array(got_log), want_log)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 def test_sweep_schedule_matches_oracle(hsg, variant):
-    """hsg_sweep = main update (both colours), n_or OR sweeps, counter,
-    renormalisation, energy log: the same composition as the oracle."""
+    """Two sweeps (heat-bath + 2 OR, renorm and E/N every sweep) against the
+    oracle: the energy log to 1e-5; per-spin differences compound through
+    the 12 half-sweep layers (each layer's output direction inherits its
+    input's round-off, amplified where fields nearly cancel), so here 90 %
+    of the spins must agree to 1e-5 and 99.9 % to 1e-3.  Exact per-layer
+    parity is the job of the half-sweep tests, exact orchestration that of
+    test_sweep_is_the_composition_of_half_sweeps."""
     L = 16
     J = inputs.gaussian_couplings(L, seed=17)
     sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=0.8, n_or=2, renorm_every=1, energy_every=1, kernel=variant)
@@ -293,7 +375,10 @@ def test_sweep_schedule_matches_oracle(hsg, variant):
     sw, ref_log = oracle.sweeps(L, inputs.round_to_f32(J), s, sch, oracle.key(17), 2)
     assert sw == 2 and len(elog) == 2
     assert np.max(np.abs(elog - ref_log)) < 1e-5
-    assert np.max(np.abs(got - s)) < 1e-4
+    err = np.max(np.abs(got - s).reshape(-1, 3), axis=1)
+    assert np.quantile(err, 0.90) <= TOL
+    assert np.quantile(err, 0.999) <= 1e-3
+    assert np.max(err) < 1e-2
 
 
 def test_long_run_energy_statistics_match_oracle(hsg):
