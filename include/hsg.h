@@ -236,6 +236,33 @@ hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t
  */
 hsg_status hsg_test_fail_alloc(int k);
 
+/*
+ * E/N of a lattice held in the caller's own device memory, without any
+ * allocation.  The paper has no counterpart: this entry point exists for
+ * callers that cannot let a library allocate device memory -- applications
+ * that give all device memory to their own arena or caching allocator at
+ * start-up and forbid raw cudaMalloc beside it, and latency-critical loops
+ * that cannot afford the device-wide synchronisation an allocation or free
+ * may cause.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * spins: device, site-major fp32 s[3*N]; J: device, site-major fp32 J[3*N]
+ * (layouts at the top of this file); e_out: device, one double, receives
+ * E/N (Eq. 1, each bond once; per-site terms fp32, sums fp64).  Queued on
+ * `cuda_stream` (NULL = legacy default stream); nothing is synchronised.
+ * L must be even and in [4, 1624]; larger or odd L is rejected with
+ * HSG_EINVAL and a message in hsg_last_error(NULL).
+ *
+ * Scratch: the per-block partial sums live in a fixed device array of
+ * HSG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  The first call on a device (with that device current)
+ * looks up the array's device address and caches it; make that first call
+ * before any stream capture.  All calls share the array: calls whose
+ * kernels overlap on the GPU (e.g. on two streams) race and must be ordered
+ * by the caller.  Errors: HSG_EINVAL, HSG_ECUDA.
+ */
+#define HSG_NOALLOC_SCRATCH_BYTES 8192
+hsg_status hsg_energy_noalloc(int L, const float* spins, const float* J, double* e_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -245,6 +245,8 @@ hsg_status grow_elog(hsg_ctx* c, int need) {
 
 }  // namespace
 
+void hsg::set_thread_error(const std::string& msg) { g_thread_error = msg; }
+
 extern "C" {
 
 hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica, void* cuda_stream) {

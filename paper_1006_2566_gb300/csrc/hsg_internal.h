@@ -4,6 +4,8 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace hsg {
@@ -47,6 +49,9 @@ cudaError_t launch_energy(const float4* S, const float* J, int L, double* partia
 
 // FP64 renormalisation of n float4 spins.  One launch.
 cudaError_t launch_renorm(float4* S, long long n, int sm_count, cudaStream_t s);
+
+// Record the calling thread's last error message (read by hsg_last_error(NULL)).
+void set_thread_error(const std::string& msg);
 
 // Philox words for counters (t, c1, c2, c3), t < n.  One launch.
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n, uint32_t* out,

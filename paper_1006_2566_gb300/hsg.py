@@ -85,6 +85,7 @@ _SIGS = {
     "hsg_version": ([], _i),
     "hsg_philox": ([_u64, _u32, _u32, _u32, _u32, _u32, _u32, _vp, _vp], _i),
     "hsg_test_fail_alloc": ([_i], _i),
+    "hsg_energy_noalloc": ([_i, _vp, _vp, _vp, _vp], _i),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -247,6 +248,19 @@ def hsg_philox(seed: int, sample: int, replica: int, c1: int, c2: int, c3: int, 
 
 def hsg_test_fail_alloc(k: int) -> None:
     _check(_lib.hsg_test_fail_alloc(int(k)))
+
+
+def hsg_energy_noalloc(L: int, spins, J, e_out, stream=None) -> None:
+    """E/N of caller-held device arrays (site-major fp32 spins and J) into the
+    device double ``e_out``, queued on ``stream``; the library allocates
+    nothing (see include/hsg.h for who needs this)."""
+    ptrs = []
+    for a in (spins, J, e_out):
+        ptr, where, _, _ = _array_ptr(a)
+        if where != HSG_DEVICE:
+            raise ValueError("hsg_energy_noalloc takes CUDA tensors")
+        ptrs.append(ptr)
+    _check(_lib.hsg_energy_noalloc(int(L), ptrs[0], ptrs[1], ptrs[2], _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------------------------
