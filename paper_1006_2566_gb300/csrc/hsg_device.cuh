@@ -102,32 +102,43 @@ __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t
 // frame of h/|h| built as in Duff et al., "Building an Orthonormal Basis,
 // Revisited" (JCGT 2017).  Uniform on S^2 when x < 1e-6.
 //
-// fp32 evaluation of log(1 + v): log1p(v) where 1 + v >= 1/2; below that
-// 1 + v = (1 - u0) + u0 e^{-2x} is summed from two positive terms (1 - u0
-// is exact), since forming 1 + v directly cancels when u0 (1 - e^{-2x})
-// is close to 1.  q = 1 - e^{-2x} comes from expm1 for small x and from
-// 1 - e^{-2x} (error <= 1 ulp of q) once e^{-2x} <= 1/2.
+// fp32 evaluation of log(1 + v): where 1 + v >= 1/2, w = 1 + v rounded and
+// log1p(v) = v log(w)/(w - 1) (Goldberg, "What every computer scientist
+// should know about floating-point arithmetic", 1991, Theorem 4: relative
+// error a few ulp); below 1/2, w = (1 - u0) + u0 e^{-2x} is summed from two
+// positive terms (1 - u0 is exact), since forming 1 + v directly cancels
+// when u0 (1 - e^{-2x}) is close to 1.  One logf serves both.  q = 1 - e^{-2x}
+// comes from expm1 for small x and from 1 - e^{-2x} once e^{-2x} <= 1/2.
+// 1/|h| is rsqrtf (2 ulp); the azimuth uses the fast sine/cosine on
+// (-pi, pi) (absolute error ~4e-7); divisions by numbers in [1e-6, 2] use
+// the fast divide (2 ulp).  Every one of these errors is below 1e-6.
 __device__ __forceinline__ float3 update_heatbath(float3 h, uint32_t site, uint32_t colour, uint32_t sweep_lo,
                                                   uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta) {
   const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_HB << 24) | (colour << 16), sweep_hi), k0, k1);
   const float u0 = u01(r.x), u1 = u01(r.y);
-  const float hn = sqrtf(dot3(h, h));
-  const float x = beta * hn;
+  const float hh = dot3(h, h);
+  const float inv = rsqrtf(hh);  // +inf for h = 0, and then x is NaN
+  const float x = beta * (hh * inv);
   if (!(x >= 1e-6f)) return sphere_point(u0, u1);
-  const float inv = 1.0f / hn;
   const float3 n = make_float3(h.x * inv, h.y * inv, h.z * inv);
   const float e2x = expf(-2.0f * x);
   const float q = e2x > 0.5f ? -expm1f(-2.0f * x) : 1.0f - e2x;
   const float v = -u0 * q;
-  const float lg = v > -0.5f ? log1pf(v) : logf(fmaf(u0, e2x, 1.0f - u0));
-  float sv = -lg / x;
+  const bool near_one = v > -0.5f;
+  const float w = near_one ? 1.0f + v : fmaf(u0, e2x, 1.0f - u0);
+  float lg = logf(w);
+  if (near_one) lg = (w == 1.0f) ? v : lg * __fdividef(v, w - 1.0f);
+  float sv = __fdividef(-lg, x);
   sv = fminf(fmaxf(sv, 0.0f), 2.0f);
   const float ct = 1.0f - sv;
-  const float st = sqrtf(fmaxf(sv * (2.0f - sv), 0.0f));
+  const float t = sv * (2.0f - sv);
+  const float st = t > 0.0f ? t * rsqrtf(t) : 0.0f;
   float sp, cp;
-  sincospif(2.0f * u1, &sp, &cp);
+  __sincosf(6.283185307179586f * (u1 - 0.5f), &sp, &cp);  // angle 2 pi u1 - pi
+  sp = -sp;
+  cp = -cp;
   const float sign = copysignf(1.0f, n.z);
-  const float a = -1.0f / (sign + n.z);
+  const float a = __fdividef(-1.0f, sign + n.z);
   const float b = n.x * n.y * a;
   const float3 e1 = make_float3(fmaf(sign * n.x * n.x, a, 1.0f), sign * b, -sign * n.x);
   const float3 e2 = make_float3(b, fmaf(n.y * n.y, a, sign), -n.y);

@@ -28,22 +28,24 @@ __device__ __forceinline__ uint32_t site_index(int xh, int p, int y, int z, int 
 // ---------------------------------------------------------------------------
 constexpr int GX = 32, GY = 8;
 
+// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.
 template <int U>
 __global__ void __launch_bounds__(GX* GY) k_half_sweep_global(const SweepArgs a) {
-  const int xh = blockIdx.x * GX + threadIdx.x;
-  const int y = blockIdx.y * GY + threadIdx.y;
-  const int z = blockIdx.z;
-  const int L = a.L, Lh = a.Lh;
+  const uint32_t xh = blockIdx.x * GX + threadIdx.x;
+  const uint32_t y = blockIdx.y * GY + threadIdx.y;
+  const uint32_t z = blockIdx.z;
+  const uint32_t L = a.L, Lh = a.Lh;
   if (xh >= Lh || y >= L) return;
-  const int p = (a.colour + y + z) & 1;  // x = 2*xh + p
-  const long long row = ((long long)z * L + y) * Lh;
-  const long long q = row + xh;
-  const long long q_xp = row + (p ? wrap_inc(xh, Lh) : xh);
-  const long long q_xm = row + (p ? xh : wrap_dec(xh, Lh));
-  const long long q_yp = ((long long)z * L + wrap_inc(y, L)) * Lh + xh;
-  const long long q_ym = ((long long)z * L + wrap_dec(y, L)) * Lh + xh;
-  const long long q_zp = ((long long)wrap_inc(z, L) * L + y) * Lh + xh;
-  const long long q_zm = ((long long)wrap_dec(z, L) * L + y) * Lh + xh;
+  const uint32_t p = (a.colour + y + z) & 1u;  // x = 2*xh + p
+  const uint32_t rowlen = Lh, plane = L * Lh;
+  const uint32_t row = (z * L + y) * Lh;
+  const uint32_t q = row + xh;
+  const uint32_t q_xp = p ? (xh + 1 == Lh ? row : q + 1) : q;
+  const uint32_t q_xm = p ? q : (xh == 0 ? row + Lh - 1 : q - 1);
+  const uint32_t q_yp = y + 1 == L ? q - (L - 1) * rowlen : q + rowlen;
+  const uint32_t q_ym = y == 0 ? q + (L - 1) * rowlen : q - rowlen;
+  const uint32_t q_zp = z + 1 == L ? q - (L - 1) * plane : q + plane;
+  const uint32_t q_zm = z == 0 ? q + (L - 1) * plane : q - plane;
 
   const float4 sxp = __ldg(a.oth + q_xp), sxm = __ldg(a.oth + q_xm);
   const float4 syp = __ldg(a.oth + q_yp), sym = __ldg(a.oth + q_ym);
