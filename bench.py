@@ -76,7 +76,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="l256_hb_or")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched"], default="l256_hb_or")
     ap.add_argument("--kernel", choices=["auto", "global", "slab"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
@@ -449,8 +449,113 @@ def run_reference(args, wl):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: many small lattices in one pool
+# ---------------------------------------------------------------------------
+
+BATCH = dict(samples=512, replicas=2, sides=(16, 24, 32, 48), seed=4, hits=4, step=0.5, n_or=2, renorm_every=10,
+             sweeps_per_step=10,
+             desc=("batched: 512 samples x 2 replicas, L uniform in {16,24,32,48} (seeded), T_s = 0.2 + 0.8 s/511, "
+                   "Gaussian J per sample (device Philox + Box-Muller), 4-hit Metropolis (ball, 0.5) + 2 OR per "
+                   "sweep, renorm every 10; one pool, one graph replay per sweep; 1 step = 10 sweeps"))
+
+
+def batch_specs():
+    """(L, seed, sample, replica, T) of every lattice of the batched workload."""
+    rng = np.random.default_rng([BATCH["seed"], 0x4C])
+    sides = rng.choice(BATCH["sides"], size=BATCH["samples"])
+    out = []
+    for s in range(BATCH["samples"]):
+        T = 0.2 + 0.8 * s / (BATCH["samples"] - 1)
+        for r in range(BATCH["replicas"]):
+            out.append((int(sides[s]), BATCH["seed"], s, r, T))
+    return out
+
+
+def run_batched(args):
+    import torch
+
+    from paper_1006_2566_gb300 import build
+
+    build.build()
+    from paper_1006_2566_gb300 import hsg
+
+    torch.cuda.set_device(0)
+    specs = batch_specs()
+    sites = sum(L ** 3 for L, *_ in specs)
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=BATCH["hits"], proposal=hsg.HSG_PROP_BALL, step=BATCH["step"],
+                         n_or=BATCH["n_or"], renorm_every=BATCH["renorm_every"])
+    sps = BATCH["sweeps_per_step"]
+    passes = 1 + BATCH["n_or"]
+    stream = torch.cuda.Stream()
+    budget = int(sum(28 * L ** 3 for L, *_ in specs) * 1.05) + (1 << 24)
+    with hsg.Pool(budget, len(specs), stream) as pool:
+        for spec in specs:
+            pool.admit(*spec)
+        t0 = time.perf_counter()
+        cfg = hsg.hsg_pool_autotune(pool.pool, sched)
+        tune_s = time.perf_counter() - t0
+        for _ in range(args.warmup):
+            pool.sweep(sched, sps)
+        torch.cuda.synchronize()
+        n0 = hsg.hsg_pool_launch_count(pool.pool)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            pool.sweep(sched, sps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = hsg.hsg_pool_launch_count(pool.pool) - n0
+        energies = pool.energies()
+    value = sites * passes * sps * args.steps / (ms * 1e6)
+    # one lattice per launch: every lattice of a representative subset swept
+    # on its own context, one after another
+    sub = specs[:: max(1, len(specs) // 64)]
+    sub_sites = sum(L ** 3 for L, *_ in sub)
+    ctxs = []
+    for (L, seed, sample, replica, T) in sub:
+        lat = hsg.Lattice(L, seed, sample, replica, stream)
+        lat.generate_couplings()
+        ctxs.append((lat, hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=BATCH["hits"], proposal=hsg.HSG_PROP_BALL,
+                                       step=BATCH["step"], n_or=BATCH["n_or"], T=T,
+                                       renorm_every=BATCH["renorm_every"])))
+    for lat, s in ctxs:
+        lat.sweep(s, 1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for lat, s in ctxs:
+        lat.sweep(s, sps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    for lat, _ in ctxs:
+        lat.close()
+    plain = sub_sites * passes * sps / (plain_ms * 1e6)
+    out = {
+        "metric": "spin updates/ns", "value": round(value, 4), "unit": "spin updates/ns", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded sides and temperatures, couplings and spins from Philox",
+        "config": {"workload": BATCH["desc"], "lattices": len(specs), "sites": sites,
+                   "autotuned": {"threads": cfg[0], "tile_sites": cfg[1], "blocks_per_sm": cfg[2],
+                                 "seconds": round(tune_s, 3)}},
+        "hit_updates_per_ns": round(sites * (BATCH["hits"] + BATCH["n_or"]) * sps * args.steps / (ms * 1e6), 4),
+        "plain_one_lattice_per_launch": {"value": round(plain, 4), "unit": "spin updates/ns",
+                                         "lattices": len(sub), "sites": sub_sites,
+                                         "ms_for_10_sweeps": round(plain_ms, 3)},
+        "speedup_vs_plain": round(value / plain, 2),
+        "gpu_launches": int(launches),
+        "energy_per_spin_mean": float(np.nanmean(energies)),
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
+    if args.workload == "batched":
+        run_batched(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

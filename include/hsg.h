@@ -147,6 +147,19 @@ hsg_status hsg_destroy(hsg_ctx* ctx);
 hsg_status hsg_set_couplings(hsg_ctx* ctx, const void* J, int dtype, int where);
 
 /*
+ * Draw the couplings on the device (Sec. 2: Gaussian J, mean 0, variance
+ * 1) from the context's (seed, sample): bond d of site i comes from the
+ * Philox draw of kind 2 at counter (i, 0, 2<<24, 0) under the key of
+ * (seed, sample, replica 0) -- the replicas of a sample share their J --
+ * through the Box-Muller transform in FP64 (J_x, J_y from (u0, u1), J_z
+ * from (u2, u3)), rounded once to FP32.  Queued on the stream.
+ * hsg_get_couplings returns the FP32 couplings site-major, J[3*i + d], in
+ * memory space `where` (HOST synchronises).
+ */
+hsg_status hsg_generate_couplings(hsg_ctx* ctx);
+hsg_status hsg_get_couplings(hsg_ctx* ctx, float* out, int where);
+
+/*
  * Run n_sweeps sweeps of `schedule` (see hsg_schedule), asynchronously on
  * the context's stream.  n_sweeps = 0 is a no-op.
  * Checkerboard half-sweeps follow Sec. 4 (non-interacting spins in
@@ -229,6 +242,69 @@ int hsg_version(void);
  */
 hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t c1, uint32_t c2, uint32_t c3,
                       uint32_t n, uint32_t* out, void* cuda_stream);
+
+/*
+ * Pools: many independent lattices (disorder samples, replicas, requests) of
+ * uneven L in one device arena, swept together.  Every half-sweep of a pool
+ * is ONE persistent kernel over a work list of (lattice, site-range) tiles
+ * covering all admitted lattices, and a sweep's launches are captured once
+ * in a CUDA graph and replayed (on a non-default stream) while lattices come
+ * and go.  Each lattice keeps its own side, Philox key, temperature and
+ * sweep counter, and is updated by the same device code with the same
+ * random numbers as a single-lattice context: its spins are bit-identical
+ * to those of the same lattice swept alone with hsg_sweep.
+ */
+typedef struct hsg_pool hsg_pool;
+
+/* A pool with an arena of `budget_bytes` of device memory (allocated once,
+ * here) and room for `max_slots` lattices, queued on `cuda_stream`.  A
+ * lattice of side L takes 28 L^3 bytes (float4 spins + 3 fp32 bonds per
+ * site), rounded up to 256.  Errors: HSG_EINVAL, HSG_ENOMEM, HSG_ECUDA. */
+hsg_status hsg_pool_create(hsg_pool** out, uint64_t budget_bytes, int max_slots, void* cuda_stream);
+hsg_status hsg_pool_destroy(hsg_pool* pool); /* NULL ok; waits for the stream */
+
+/* Admit one lattice: side L (even, 4..1624), Philox key from (seed,
+ * sample, replica), temperature T (> 0, inf allowed); spins start as in
+ * hsg_create; couplings from J (site-major, dtype / where as in
+ * hsg_set_couplings) or, with J == NULL, generated on the device as by
+ * hsg_generate_couplings.  *slot receives the lattice's slot index, its
+ * sweep counter starts at 0.  HSG_EBUSY (nothing changed) when no slot is
+ * free or the arena has no free block large enough. */
+hsg_status hsg_pool_admit(hsg_pool* pool, int L, uint64_t seed, uint32_t sample, uint32_t replica, double T,
+                          const void* J, int dtype, int where, int* slot);
+
+/* Release a lattice's slot and arena block (waits for queued work). */
+hsg_status hsg_pool_retire(hsg_pool* pool, int slot);
+
+/* n_sweeps sweeps of every admitted lattice, each at its own temperature
+ * (schedule.T and schedule.kernel are ignored; energy_every must be 0;
+ * renorm_every applies to each lattice's own counter).  Asynchronous. */
+hsg_status hsg_pool_sweep(hsg_pool* pool, const hsg_schedule* schedule, int n_sweeps);
+
+/* E/N of every slot into out[0..n) (NaN for free slots); FP32 site terms,
+ * FP64 sums, fixed order.  Synchronises. */
+hsg_status hsg_pool_energies(hsg_pool* pool, double* out, int n);
+
+/* One lattice's spins, site-major fp32 (as hsg_get_spins), and counter. */
+hsg_status hsg_pool_get_spins(hsg_pool* pool, int slot, float* out, int where);
+hsg_status hsg_pool_get_sweep(hsg_pool* pool, int slot, uint64_t* sweep);
+
+/* Arena bytes in use, the budget, and the number of admitted lattices. */
+hsg_status hsg_pool_usage(hsg_pool* pool, uint64_t* bytes_used, uint64_t* bytes_budget, int* active);
+
+/* Launch configuration of the pool kernels: threads per CTA (64, 128 or
+ * 256), sites per tile (a multiple of threads, <= 8192) and CTAs per SM of
+ * the persistent grid (1..32).  hsg_pool_autotune times every candidate on
+ * the admitted lattices (one warm-up and two timed sweeps each), restores
+ * the lattices and counters afterwards, keeps the fastest configuration and
+ * reports it.  Results do not depend on the configuration. */
+hsg_status hsg_pool_config(hsg_pool* pool, int threads, int tile_sites, int blocks_per_sm);
+hsg_status hsg_pool_autotune(hsg_pool* pool, const hsg_schedule* schedule, int* threads, int* tile_sites,
+                             int* blocks_per_sm);
+
+/* Kernel launches issued for this pool (graph replays count their kernels). */
+hsg_status hsg_pool_launch_count(hsg_pool* pool, uint64_t* launches);
+const char* hsg_pool_last_error(const hsg_pool* pool);
 
 /*
  * Fault injection for tests: the k-th device allocation from now (k >= 1)

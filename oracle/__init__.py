@@ -79,6 +79,7 @@ def _load():
         lib.oracle_u01.restype = ctypes.c_double
         lib.oracle_colour.argtypes = [ctypes.c_int, ctypes.c_int64]
         lib.oracle_init_spins.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _dp]
+        lib.oracle_gaussian_couplings.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, _dp]
         lib.oracle_local_field.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int64, _dp]
         lib.oracle_energy.argtypes = [ctypes.c_int, _dp, _dp]
         lib.oracle_energy.restype = ctypes.c_double
@@ -173,6 +174,13 @@ def init_spins(L: int, seed: int, sample: int = 0, replica: int = 0) -> np.ndarr
     s = np.zeros(3 * L ** 3, dtype=np.float64)
     _load().oracle_init_spins(int(L), int(seed), int(sample), int(replica), _d(s))
     return s
+
+
+def gaussian_couplings(L: int, seed: int, sample: int = 0) -> np.ndarray:
+    """J ~ N(0,1) from Philox (kind JGEN) and Box-Muller, site-major."""
+    J = np.zeros(3 * L ** 3, dtype=np.float64)
+    _load().oracle_gaussian_couplings(int(L), int(seed), int(sample), _d(J))
+    return J
 
 
 def local_field(L: int, J: np.ndarray, s: np.ndarray, i: int) -> np.ndarray:

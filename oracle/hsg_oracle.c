@@ -176,6 +176,30 @@ void oracle_init_spins(int L, uint64_t seed, uint32_t sample, uint32_t replica, 
   }
 }
 
+/* Gaussian couplings J ~ N(0,1) (Sec. 2: Gaussian, mean 0, variance 1),
+ * drawn from Philox so that a sample's disorder needs no host-side arrays:
+ * site i draws (u0,u1,u2,u3) at counter (i, 0, JGEN<<24, 0) under the key of
+ * (seed, sample, replica 0) -- replicas of a sample share J -- and the
+ * Box-Muller transform (Box & Muller, Ann. Math. Stat. 29, 1958) gives
+ *   J[3i]   = sqrt(-2 ln u0) cos(2 pi u1),
+ *   J[3i+1] = sqrt(-2 ln u0) sin(2 pi u1),
+ *   J[3i+2] = sqrt(-2 ln u2) cos(2 pi u3). */
+void oracle_gaussian_couplings(int L, uint64_t seed, uint32_t sample, double* J) {
+  uint32_t key[2], ctr[4], r[4];
+  int64_t n = (int64_t)L * L * L;
+  oracle_key(seed, sample, 0, key);
+  for (int64_t i = 0; i < n; ++i) {
+    oracle_counter((uint32_t)i, 0, ORACLE_KIND_JGEN, 0, 0, ctr);
+    oracle_philox4x32_10(ctr, key, r);
+    double u0 = oracle_u01(r[0]), u1 = oracle_u01(r[1]);
+    double u2 = oracle_u01(r[2]), u3 = oracle_u01(r[3]);
+    double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
+    J[3 * i] = a * cos(2.0 * ORACLE_PI * u1);
+    J[3 * i + 1] = a * sin(2.0 * ORACLE_PI * u1);
+    J[3 * i + 2] = b * cos(2.0 * ORACLE_PI * u3);
+  }
+}
+
 /* Local field of site i (Eq. 2 with reading R2):
  * h_i = sum_d ( J[3i+d] s_{i+e_d} + J[3(i-e_d)+d] s_{i-e_d} ). */
 void oracle_local_field(int L, const double* J, const double* s, int64_t i, double h[3]) {

@@ -349,6 +349,39 @@ hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
   return HSG_OK;
 }
 
+hsg_status hsg_generate_couplings(hsg_ctx* c) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  // Key of (seed, sample, replica 0): replicas of one sample share J.
+  const uint32_t k1 = (uint32_t)(c->seed >> 32) ^ ((2u * c->sample) * 0x9E3779B9u);
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling generator kernel",
+                         [&] { return hsg::launch_gen_couplings(c->J, c->L, c->k0, k1, c->stream); });
+  if (st == HSG_OK) c->have_J = true;
+  return st;
+}
+
+hsg_status hsg_get_couplings(hsg_ctx* c, float* out, int where) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!out) return fail(c, HSG_EINVAL, "out is NULL");
+  if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
+  if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
+  const size_t bytes = sizeof(float) * 3 * (size_t)c->N;
+  float* dst = out;
+  if (where == HSG_HOST) {
+    hsg_status st = ensure_stage(c, bytes);
+    if (st != HSG_OK) return st;
+    dst = static_cast<float*>(c->stage);
+  }
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling gather kernel",
+                         [&] { return hsg::launch_gather_couplings(c->J, dst, c->L, c->stream); });
+  if (st != HSG_OK) return st;
+  if (where == HSG_HOST) {
+    cudaError_t e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "coupling readback");
+  }
+  return HSG_OK;
+}
+
 hsg_status hsg_sweep(hsg_ctx* c, const hsg_schedule* s, int n_sweeps) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
   hsg_status st = check_schedule(c, s, true);

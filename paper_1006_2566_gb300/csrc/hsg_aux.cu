@@ -45,6 +45,46 @@ __global__ void k_scatter_couplings(const T* __restrict__ src, float* __restrict
   for (int d = 0; d < 3; ++d) J[(2 * d + c) * nh + q] = (float)src[3 * i + d];
 }
 
+// Gaussian couplings from Philox kind JGEN (key of (seed, sample), shared by
+// the replicas): site i draws (u0..u3) at counter (i, 0, JGEN<<24, 0) and the
+// Box-Muller transform (Box & Muller 1958) in fp64 gives its +x, +y, +z bonds
+// sqrt(-2 ln u0) cos(2 pi u1), sqrt(-2 ln u0) sin(2 pi u1), sqrt(-2 ln u2)
+// cos(2 pi u3), each rounded once to fp32.  Thread per site (x, y, z).
+__global__ void k_gen_couplings(float* __restrict__ J, int L, uint32_t k0, uint32_t k1) {
+  const int x = blockIdx.x * 64 + threadIdx.x;
+  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L || y >= L) return;
+  const int Lh = L / 2;
+  const long long nh = (long long)L * L * Lh;
+  const uint32_t i = (uint32_t)x + (uint32_t)y * L + (uint32_t)z * L * L;
+  const int c = (x + y + z) & 1;
+  const long long q = ((long long)z * L + y) * Lh + (x >> 1);
+  const uint4 r = philox4x32_10(make_uint4(i, 0u, KIND_JGEN << 24, 0u), k0, k1);
+  const double u0 = u01(r.x), u1 = u01(r.y), u2 = u01(r.z), u3 = u01(r.w);
+  const double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
+  double s1, c1;
+  sincospi(2.0 * u1, &s1, &c1);
+  J[(0 + c) * nh + q] = (float)(a * c1);
+  J[(2 + c) * nh + q] = (float)(a * s1);
+  J[(4 + c) * nh + q] = (float)(b * cospi(2.0 * u3));
+}
+
+// Colour-split couplings -> site-major fp32.  Thread per site (x, y, z).
+__global__ void k_gather_couplings(const float* __restrict__ J, float* __restrict__ dst, int L) {
+  const int x = blockIdx.x * 64 + threadIdx.x;
+  const int y = blockIdx.y * 4 + threadIdx.y;
+  const int z = blockIdx.z;
+  if (x >= L || y >= L) return;
+  const int Lh = L / 2;
+  const long long nh = (long long)L * L * Lh;
+  const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
+  const int c = (x + y + z) & 1;
+  const long long q = ((long long)z * L + y) * Lh + (x >> 1);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dst[3 * i + d] = J[(2 * d + c) * nh + q];
+}
+
 __global__ void k_scatter_spins(const float* __restrict__ src, float4* __restrict__ S, int L) {
   const int x = blockIdx.x * 64 + threadIdx.x;
   const int y = blockIdx.y * 4 + threadIdx.y;
@@ -139,33 +179,10 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_energy_final(const double* __
   }
 }
 
-// Renormalisation s <- s/|s|.  d = |s|^2 - 1 is formed in fp64 from the
-// exact squares of the fp32 components (three FMAs, error ~1e-16).  Spins
-// drift from unit length only by fp32 round-off, so |d| is tiny and
-// 1/sqrt(1+d) - 1 = -d/2 + 3d^2/8 - 5d^3/16 + O(d^4) (binomial series; for
-// |d| < 2^-8 the remainder is below 2^-33) is evaluated in fp32 and applied
-// as s + s*c with one rounding: the result is within a hair of the
-// correctly rounded s/|s|.  Larger |d| takes the fp64 reciprocal square
-// root; a zero spin is left as is.
+// Renormalisation of every spin (renorm_spin, hsg_device.cuh).
 __global__ void k_renorm(float4* __restrict__ S, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    float4 v = S[t];
-    const double dx = v.x, dy = v.y, dz = v.z;
-    const double d = fma(dx, dx, fma(dy, dy, fma(dz, dz, -1.0)));
-    const float df = (float)d;
-    if (fabsf(df) < 0x1p-8f) {
-      const float c = df * fmaf(df, fmaf(df, -0.3125f, 0.375f), -0.5f);
-      v.x = fmaf(v.x, c, v.x);
-      v.y = fmaf(v.y, c, v.y);
-      v.z = fmaf(v.z, c, v.z);
-    } else if (d > -1.0) {
-      const double r = rsqrt(d + 1.0);
-      v.x = (float)(dx * r);
-      v.y = (float)(dy * r);
-      v.z = (float)(dz * r);
-    }
-    S[t] = v;
-  }
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    S[t] = renorm_spin(S[t]);
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n,
@@ -187,6 +204,16 @@ cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L,
     k_scatter_couplings<double><<<grid, block, 0, s>>>(static_cast<const double*>(src), J, L);
   else
     k_scatter_couplings<float><<<grid, block, 0, s>>>(static_cast<const float*>(src), J, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gen_couplings(float* J, int L, uint32_t k0, uint32_t k1, cudaStream_t s) {
+  k_gen_couplings<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(J, L, k0, k1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_couplings(const float* J, float* dst, int L, cudaStream_t s) {
+  k_gather_couplings<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(J, dst, L);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,7 @@ namespace hsg {
 enum UpdKind : int { U_OR = 0, U_MET_SPHERE = 1, U_MET_BALL = 2, U_HB = 3 };
 
 // Philox stream kinds (third counter word, bits 24..31).
-constexpr uint32_t KIND_INIT = 1u, KIND_MET = 3u, KIND_HB = 4u;
+constexpr uint32_t KIND_INIT = 1u, KIND_JGEN = 2u, KIND_MET = 3u, KIND_HB = 4u;
 
 // Philox-4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of the
 // 4x32 multiply/xor bijection; the key is bumped by the Weyl increments
@@ -172,6 +172,73 @@ __device__ __forceinline__ float3 update_site(float3 s, float3 h, uint32_t site,
   } else {
     return update_heatbath(h, site, colour, sweep_lo, sweep_hi, k0, k1, beta);
   }
+}
+
+// Renormalisation s <- s/|s|.  d = |s|^2 - 1 is formed in fp64 from the
+// exact squares of the fp32 components (three FMAs, error ~1e-16).  Spins
+// drift from unit length only by fp32 round-off, so |d| is tiny and
+// 1/sqrt(1+d) - 1 = -d/2 + 3d^2/8 - 5d^3/16 + O(d^4) (binomial series; for
+// |d| < 2^-8 the remainder is below 2^-33) is evaluated in fp32 and applied
+// as s + s*c with one rounding: the result is within a hair of the
+// correctly rounded s/|s|.  Larger |d| takes the fp64 reciprocal square
+// root; a zero spin is left as is.
+__device__ __forceinline__ float4 renorm_spin(float4 v) {
+  const double dx = v.x, dy = v.y, dz = v.z;
+  const double d = fma(dx, dx, fma(dy, dy, fma(dz, dz, -1.0)));
+  const float df = (float)d;
+  if (fabsf(df) < 0x1p-8f) {
+    const float c = df * fmaf(df, fmaf(df, -0.3125f, 0.375f), -0.5f);
+    v.x = fmaf(v.x, c, v.x);
+    v.y = fmaf(v.y, c, v.y);
+    v.z = fmaf(v.z, c, v.z);
+  } else if (d > -1.0) {
+    const double r = rsqrt(d + 1.0);
+    v.x = (float)(dx * r);
+    v.y = (float)(dy * r);
+    v.z = (float)(dz * r);
+  }
+  return v;
+}
+
+// One site of a half-sweep: site (x = 2 xh + p, y, z) of colour `colour`
+// gathers its six other-colour neighbours and bonds (layout at the top of
+// this file), forms h (Eq. 2), applies update U and stores its new spin.
+// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.  Shared by every
+// half-sweep kernel that updates one site per thread, so that they give
+// bit-identical results.
+template <int U>
+__device__ __forceinline__ void half_sweep_site(float4* __restrict__ own, const float4* __restrict__ oth,
+                                                const float* __restrict__ jx_own, const float* __restrict__ jy_own,
+                                                const float* __restrict__ jz_own, const float* __restrict__ jx_oth,
+                                                const float* __restrict__ jy_oth, const float* __restrict__ jz_oth,
+                                                uint32_t xh, uint32_t y, uint32_t z, uint32_t L, uint32_t Lh,
+                                                uint32_t colour, uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
+                                                uint32_t k1, float beta, float step, int hits) {
+  const uint32_t p = (colour + y + z) & 1u;  // x = 2*xh + p
+  const uint32_t plane = L * Lh;
+  const uint32_t row = (z * L + y) * Lh;
+  const uint32_t q = row + xh;
+  const uint32_t q_xp = p ? (xh + 1 == Lh ? row : q + 1) : q;
+  const uint32_t q_xm = p ? q : (xh == 0 ? row + Lh - 1 : q - 1);
+  const uint32_t q_yp = y + 1 == L ? q - (L - 1) * Lh : q + Lh;
+  const uint32_t q_ym = y == 0 ? q + (L - 1) * Lh : q - Lh;
+  const uint32_t q_zp = z + 1 == L ? q - (L - 1) * plane : q + plane;
+  const uint32_t q_zm = z == 0 ? q + (L - 1) * plane : q - plane;
+  const float4 sxp = __ldg(oth + q_xp), sxm = __ldg(oth + q_xm);
+  const float4 syp = __ldg(oth + q_yp), sym = __ldg(oth + q_ym);
+  const float4 szp = __ldg(oth + q_zp), szm = __ldg(oth + q_zm);
+  const float jxp = __ldg(jx_own + q), jxm = __ldg(jx_oth + q_xm);
+  const float jyp = __ldg(jy_own + q), jym = __ldg(jy_oth + q_ym);
+  const float jzp = __ldg(jz_own + q), jzm = __ldg(jz_oth + q_zm);
+  float3 s = make_float3(0.0f, 0.0f, 0.0f);
+  if constexpr (U != U_HB) {
+    const float4 o = own[q];
+    s = make_float3(o.x, o.y, o.z);
+  }
+  const float3 h = local_field(sxp, sxm, syp, sym, szp, szm, jxp, jxm, jyp, jym, jzp, jzm);
+  const uint32_t site = (2 * xh + p) + y * L + z * L * L;
+  const float3 t = update_site<U>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  own[q] = make_float4(t.x, t.y, t.z, 0.0f);
 }
 
 __device__ __forceinline__ int wrap_inc(int v, int n) { return v + 1 == n ? 0 : v + 1; }

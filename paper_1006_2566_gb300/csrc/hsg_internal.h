@@ -38,6 +38,11 @@ cudaError_t launch_init_spins(float4* S, int L, uint32_t k0, uint32_t k1, cudaSt
 // Site-major -> colour-split couplings (src: 3N fp32 or fp64).  One launch.
 cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s);
 
+// Gaussian couplings from Philox kind JGEN under key (k0, k1), written
+// colour-split; and colour-split -> site-major fp32 couplings.  One launch each.
+cudaError_t launch_gen_couplings(float* J, int L, uint32_t k0, uint32_t k1, cudaStream_t s);
+cudaError_t launch_gather_couplings(const float* J, float* dst, int L, cudaStream_t s);
+
 // Site-major fp32 spins <-> colour-split float4 spins.  One launch each.
 cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_t s);
 cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s);

@@ -66,6 +66,8 @@ _SIGS = {
     "hsg_create": ([ctypes.POINTER(_vp), _i, _u64, _u32, _u32, _vp], _i),
     "hsg_destroy": ([_vp], _i),
     "hsg_set_couplings": ([_vp, _vp, _i, _i], _i),
+    "hsg_generate_couplings": ([_vp], _i),
+    "hsg_get_couplings": ([_vp, _vp, _i], _i),
     "hsg_sweep": ([_vp, _sch_p, _i], _i),
     "hsg_energy": ([_vp, ctypes.POINTER(_d)], _i),
     "hsg_get_energy_log": ([_vp, ctypes.POINTER(_d), _i, ctypes.POINTER(_i)], _i),
@@ -86,6 +88,19 @@ _SIGS = {
     "hsg_philox": ([_u64, _u32, _u32, _u32, _u32, _u32, _u32, _vp, _vp], _i),
     "hsg_test_fail_alloc": ([_i], _i),
     "hsg_energy_noalloc": ([_i, _vp, _vp, _vp, _vp], _i),
+    "hsg_pool_create": ([ctypes.POINTER(_vp), _u64, _i, _vp], _i),
+    "hsg_pool_destroy": ([_vp], _i),
+    "hsg_pool_admit": ([_vp, _i, _u64, _u32, _u32, _d, _vp, _i, _i, ctypes.POINTER(_i)], _i),
+    "hsg_pool_retire": ([_vp, _i], _i),
+    "hsg_pool_sweep": ([_vp, _sch_p, _i], _i),
+    "hsg_pool_energies": ([_vp, ctypes.POINTER(_d), _i], _i),
+    "hsg_pool_get_spins": ([_vp, _i, _vp, _i], _i),
+    "hsg_pool_get_sweep": ([_vp, _i, ctypes.POINTER(_u64)], _i),
+    "hsg_pool_usage": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_i)], _i),
+    "hsg_pool_config": ([_vp, _i, _i, _i], _i),
+    "hsg_pool_autotune": ([_vp, _sch_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "hsg_pool_launch_count": ([_vp, ctypes.POINTER(_u64)], _i),
+    "hsg_pool_last_error": ([_vp], ctypes.c_char_p),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -149,6 +164,17 @@ def hsg_set_couplings(ctx, J) -> None:
     if code is None:
         raise TypeError("couplings must be float32 or float64")
     _check(_lib.hsg_set_couplings(ctx, ptr, code, where), ctx)
+
+
+def hsg_generate_couplings(ctx) -> None:
+    _check(_lib.hsg_generate_couplings(ctx), ctx)
+
+
+def hsg_get_couplings(ctx, out) -> None:
+    ptr, where, code, _ = _array_ptr(out)
+    if code != HSG_F32:
+        raise TypeError("couplings are read back as float32")
+    _check(_lib.hsg_get_couplings(ctx, ptr, where), ctx)
 
 
 def hsg_sweep(ctx, sched: hsg_schedule, n_sweeps: int) -> None:
@@ -295,6 +321,14 @@ class Lattice:
     def set_couplings(self, J) -> None:
         hsg_set_couplings(self.ctx, J)
 
+    def generate_couplings(self) -> None:
+        hsg_generate_couplings(self.ctx)
+
+    def couplings(self) -> np.ndarray:
+        out = np.zeros(3 * self.N, dtype=np.float32)
+        hsg_get_couplings(self.ctx, out)
+        return out
+
     def sweep(self, sched: hsg_schedule, n_sweeps: int = 1) -> None:
         hsg_sweep(self.ctx, sched, n_sweeps)
 
@@ -325,3 +359,143 @@ class Lattice:
     @sweep_count.setter
     def sweep_count(self, v: int) -> None:
         hsg_set_sweep(self.ctx, v)
+
+
+# ---------------------------------------------------------------------------
+# Pools (many lattices swept together)
+# ---------------------------------------------------------------------------
+
+def _pcheck(status: int, pool) -> None:
+    if status != HSG_OK:
+        raise HsgError(status, _lib.hsg_pool_last_error(pool).decode() or _lib.hsg_last_error(None).decode())
+
+
+def hsg_pool_create(budget_bytes: int, max_slots: int, stream=None) -> ctypes.c_void_p:
+    pool = _vp()
+    _check(_lib.hsg_pool_create(ctypes.byref(pool), int(budget_bytes), int(max_slots), _stream_ptr(stream)))
+    return pool
+
+
+def hsg_pool_destroy(pool) -> None:
+    _check(_lib.hsg_pool_destroy(pool))
+
+
+def hsg_pool_admit(pool, L: int, seed: int, sample: int = 0, replica: int = 0, T: float = 1.0, J=None) -> int:
+    """Admit a lattice; J None draws the couplings on the device.  Raises
+    HsgError with status HSG_EBUSY when the pool is full."""
+    slot = _i(-1)
+    if J is None:
+        ptr, code, where = None, HSG_F32, HSG_DEVICE
+    else:
+        ptr, where, code, _ = _array_ptr(J)
+        if code is None:
+            raise TypeError("couplings must be float32 or float64")
+    _pcheck(_lib.hsg_pool_admit(pool, int(L), int(seed), int(sample), int(replica), float(T), ptr, code, where,
+                                ctypes.byref(slot)), pool)
+    return slot.value
+
+
+def hsg_pool_retire(pool, slot: int) -> None:
+    _pcheck(_lib.hsg_pool_retire(pool, int(slot)), pool)
+
+
+def hsg_pool_sweep(pool, sched: hsg_schedule, n_sweeps: int) -> None:
+    _pcheck(_lib.hsg_pool_sweep(pool, ctypes.byref(sched), int(n_sweeps)), pool)
+
+
+def hsg_pool_energies(pool, n: int) -> np.ndarray:
+    out = np.zeros(int(n), dtype=np.float64)
+    _pcheck(_lib.hsg_pool_energies(pool, out.ctypes.data_as(ctypes.POINTER(_d)), int(n)), pool)
+    return out
+
+
+def hsg_pool_get_spins(pool, slot: int, out) -> None:
+    ptr, where, code, _ = _array_ptr(out)
+    if code != HSG_F32:
+        raise TypeError("spins are float32")
+    _pcheck(_lib.hsg_pool_get_spins(pool, int(slot), ptr, where), pool)
+
+
+def hsg_pool_get_sweep(pool, slot: int) -> int:
+    v = _u64(0)
+    _pcheck(_lib.hsg_pool_get_sweep(pool, int(slot), ctypes.byref(v)), pool)
+    return v.value
+
+
+def hsg_pool_usage(pool):
+    used, budget, active = _u64(0), _u64(0), _i(0)
+    _pcheck(_lib.hsg_pool_usage(pool, ctypes.byref(used), ctypes.byref(budget), ctypes.byref(active)), pool)
+    return used.value, budget.value, active.value
+
+
+def hsg_pool_config(pool, threads: int, tile_sites: int, blocks_per_sm: int) -> None:
+    _pcheck(_lib.hsg_pool_config(pool, int(threads), int(tile_sites), int(blocks_per_sm)), pool)
+
+
+def hsg_pool_autotune(pool, sched: hsg_schedule):
+    t, ts, b = _i(0), _i(0), _i(0)
+    _pcheck(_lib.hsg_pool_autotune(pool, ctypes.byref(sched), ctypes.byref(t), ctypes.byref(ts), ctypes.byref(b)),
+            pool)
+    return t.value, ts.value, b.value
+
+
+def hsg_pool_launch_count(pool) -> int:
+    v = _u64(0)
+    _pcheck(_lib.hsg_pool_launch_count(pool, ctypes.byref(v)), pool)
+    return v.value
+
+
+def hsg_pool_last_error(pool) -> str:
+    return _lib.hsg_pool_last_error(pool).decode()
+
+
+class Pool:
+    """Many lattices in one device arena (a thin wrapper over hsg_pool_*)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int, stream=None):
+        self.pool = hsg_pool_create(budget_bytes, max_slots, stream)
+        self.max_slots = int(max_slots)
+        self.sides: dict[int, int] = {}
+
+    def close(self) -> None:
+        if self.pool is not None and self.pool.value:
+            hsg_pool_destroy(self.pool)
+        self.pool = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def admit(self, L, seed, sample=0, replica=0, T=1.0, J=None) -> int:
+        slot = hsg_pool_admit(self.pool, L, seed, sample, replica, T, J)
+        self.sides[slot] = int(L)
+        return slot
+
+    def retire(self, slot: int) -> None:
+        hsg_pool_retire(self.pool, slot)
+        self.sides.pop(slot, None)
+
+    def sweep(self, sched: hsg_schedule, n_sweeps: int = 1) -> None:
+        hsg_pool_sweep(self.pool, sched, n_sweeps)
+
+    def energies(self) -> np.ndarray:
+        return hsg_pool_energies(self.pool, self.max_slots)
+
+    def spins(self, slot: int) -> np.ndarray:
+        out = np.zeros(3 * self.sides[slot] ** 3, dtype=np.float32)
+        hsg_pool_get_spins(self.pool, slot, out)
+        return out
+
+    def sweep_count(self, slot: int) -> int:
+        return hsg_pool_get_sweep(self.pool, slot)
+
+    def usage(self):
+        return hsg_pool_usage(self.pool)

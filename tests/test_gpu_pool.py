@@ -1,0 +1,189 @@
+"""Device coupling generator and pools of lattices (needs a CUDA GPU).
+
+A lattice swept inside a pool must be bit-identical to the same lattice
+(same key, temperature, couplings) swept alone through a context, whatever
+else is admitted or retired around it and whatever launch configuration the
+pool uses: same device code, same random numbers.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_1006_2566_gb300 import inputs  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def hsg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1006_2566_gb300 import build
+
+    build.build()
+    oracle.build()
+    from paper_1006_2566_gb300 import hsg as h
+
+    return h
+
+
+# ---------------------------------------------------------------------------
+# Couplings on the device
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,seed,sample", [(8, 4, 7), (24, 1, 0), (40, 9, 3)])
+def test_generated_couplings_match_oracle(hsg, L, seed, sample):
+    """Both sides evaluate Box-Muller in fp64 from the same Philox words;
+    the device rounds once to fp32, so the values agree to the last bit
+    except where the two fp64 results straddle an fp32 rounding boundary."""
+    with hsg.Lattice(L, seed, sample, replica=1) as lat:
+        lat.generate_couplings()
+        got = lat.couplings()
+    ref = oracle.gaussian_couplings(L, seed, sample).astype(np.float32)
+    assert np.mean(got == ref) > 0.9999
+    np.testing.assert_array_max_ulp(got, ref, maxulp=1)
+
+
+def test_coupling_upload_round_trip(hsg):
+    L = 12
+    J = inputs.gaussian_couplings(L, 3, dtype=np.float32)
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_couplings(J)
+        assert np.array_equal(lat.couplings(), J)
+        lat.set_couplings(J.astype(np.float64))
+        assert np.array_equal(lat.couplings(), J)
+
+
+# ---------------------------------------------------------------------------
+# Pools
+# ---------------------------------------------------------------------------
+
+SPECS = [  # (L, seed, sample, replica, T)
+    (4, 11, 0, 0, 0.5),
+    (6, 11, 0, 1, 0.5),
+    (16, 11, 1, 0, 1.0),
+    (24, 11, 2, 0, 0.3),
+    (8, 11, 3, 1, math.inf),
+    (40, 11, 4, 0, 0.7),
+]
+
+
+def base_schedule(hsg, kind):
+    k = hsg.HSG_METROPOLIS if kind == "MET" else hsg.HSG_HEATBATH
+    return dict(kind=k, hits=3, proposal=hsg.HSG_PROP_BALL, step=0.5, n_or=2, renorm_every=2)
+
+
+def run_alone(hsg, spec, sched_kw, n, J=None):
+    L, seed, sample, replica, T = spec
+    with hsg.Lattice(L, seed, sample, replica) as lat:
+        if J is None:
+            lat.generate_couplings()
+        else:
+            lat.set_couplings(J)
+        lat.sweep(hsg.schedule(T=T, **sched_kw), n)
+        return lat.spins(), lat.energy()
+
+
+@pytest.mark.parametrize("kind", ["MET", "HB"])
+@pytest.mark.parametrize("use_stream", [True, False])
+def test_pool_lattices_are_bit_identical_to_lattices_alone(hsg, kind, use_stream):
+    kw = base_schedule(hsg, kind)
+    stream = torch.cuda.Stream() if use_stream else None  # graph replay / direct launches
+    with hsg.Pool(1 << 28, 16, stream) as pool:
+        slots = [pool.admit(*spec) for spec in SPECS]
+        pool.sweep(hsg.schedule(**kw), 3)
+        late = pool.admit(12, 11, 9, 0, 0.9)  # admitted mid-run: the work list changes
+        pool.retire(slots[1])  # and one retired
+        pool.sweep(hsg.schedule(**kw), 2)
+        e = pool.energies()
+        assert math.isnan(e[slots[1]])
+        for slot, spec in zip(slots, SPECS):
+            if slot == slots[1]:
+                continue
+            want, want_e = run_alone(hsg, spec, kw, 5)
+            assert np.array_equal(pool.spins(slot), want), spec
+            assert abs(e[slot] - want_e) <= 2e-6
+            assert pool.sweep_count(slot) == 5
+        want, _ = run_alone(hsg, (12, 11, 9, 0, 0.9), kw, 2)
+        assert np.array_equal(pool.spins(late), want)
+        assert pool.sweep_count(late) == 2
+
+
+def test_pool_with_host_couplings(hsg):
+    kw = base_schedule(hsg, "MET")
+    J = inputs.gaussian_couplings(10, seed=5)
+    with hsg.Pool(1 << 24, 4, torch.cuda.Stream()) as pool:
+        s = pool.admit(10, 5, 0, 0, 0.6, J=J)
+        pool.sweep(hsg.schedule(**kw), 3)
+        got = pool.spins(s)
+    want, _ = run_alone(hsg, (10, 5, 0, 0, 0.6), kw, 3, J=J)
+    assert np.array_equal(got, want)
+
+
+def test_pool_results_do_not_depend_on_launch_configuration(hsg):
+    kw = base_schedule(hsg, "HB")
+    outs = []
+    for cfg in [(64, 64, 2), (256, 2048, 16), (128, 384, 5)]:
+        with hsg.Pool(1 << 28, 8, torch.cuda.Stream()) as pool:
+            hsg.hsg_pool_config(pool.pool, *cfg)
+            slots = [pool.admit(*spec) for spec in SPECS]
+            pool.sweep(hsg.schedule(**kw), 3)
+            outs.append([pool.spins(s) for s in slots])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
+    for a, b in zip(outs[0], outs[2]):
+        assert np.array_equal(a, b)
+
+
+def test_pool_autotune_restores_state_and_keeps_results(hsg):
+    kw = base_schedule(hsg, "MET")
+    with hsg.Pool(1 << 28, 8, torch.cuda.Stream()) as pool:
+        slots = [pool.admit(*spec) for spec in SPECS]
+        pool.sweep(hsg.schedule(**kw), 2)
+        before = [pool.spins(s) for s in slots]
+        cfg = hsg.hsg_pool_autotune(pool.pool, hsg.schedule(**kw))
+        assert cfg[0] in (128, 256) and cfg[1] % cfg[0] == 0 and cfg[2] >= 1
+        for s, b in zip(slots, before):
+            assert np.array_equal(pool.spins(s), b)
+            assert pool.sweep_count(s) == 2
+        pool.sweep(hsg.schedule(**kw), 2)
+        for s, spec in zip(slots, SPECS):
+            want, _ = run_alone(hsg, spec, kw, 4)
+            assert np.array_equal(pool.spins(s), want)
+
+
+def test_pool_admission_by_budget_and_slots(hsg):
+    per = 28 * 16 ** 3  # bytes of one L = 16 lattice (a multiple of 256)
+    with hsg.Pool(2 * per, 3, torch.cuda.Stream()) as pool:
+        a = pool.admit(16, 1, 0)
+        b = pool.admit(16, 1, 1)
+        assert pool.usage() == (2 * per, 2 * per, 2)
+        with pytest.raises(hsg.HsgError) as e:
+            pool.admit(16, 1, 2)
+        assert e.value.status == hsg.HSG_EBUSY
+        pool.retire(a)
+        c = pool.admit(8, 1, 3)
+        d = pool.admit(8, 1, 4)  # two small ones fit in the freed block
+        with pytest.raises(hsg.HsgError) as e:
+            pool.admit(4, 1, 5)  # no free slot left (3 of 3)
+        assert e.value.status == hsg.HSG_EBUSY
+        pool.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, n_or=1), 1)
+        for bad in (dict(L=7), dict(L=2), dict(L=2000), dict(T=0.0)):
+            args = dict(L=8, seed=1, sample=9, replica=0, T=1.0)
+            args.update(bad)
+            with pytest.raises(hsg.HsgError) as e:
+                pool.admit(**args)
+            assert e.value.status in (hsg.HSG_EINVAL, hsg.HSG_EBUSY)
+        with pytest.raises(hsg.HsgError) as e:
+            pool.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, energy_every=1), 1)
+        assert e.value.status == hsg.HSG_EINVAL
+        assert c == a  # the freed slot index is reused
+        pool.retire(d)
+        with pytest.raises(hsg.HsgError):
+            pool.retire(d)  # already free
+        with pytest.raises(hsg.HsgError):
+            pool.retire(7)  # no such slot
+        assert len({b, c, d}) == 3

@@ -468,3 +468,21 @@ def test_ball_proposal_matches_rejection_sampled_ball(orc):
     v = np.array([0.0, 0.0, 1.0]) + 0.5 * ball
     ref = v[:, 2] / np.linalg.norm(v, axis=1)
     assert stats.ks_2samp(got, ref).pvalue > 1e-3
+
+
+def test_gaussian_couplings_are_standard_normal(orc):
+    """Philox + Box-Muller couplings: KS against N(0,1), mean 0, variance 1,
+    the two members of a Box-Muller pair uncorrelated, even fourth moment 3;
+    distinct samples give distinct disorder, the same sample the same."""
+    L = 16
+    J = orc.gaussian_couplings(L, seed=4, sample=7)
+    n = J.size
+    assert stats.kstest(J, stats.norm.cdf).pvalue > 1e-3
+    assert abs(J.mean()) < 4 / np.sqrt(n)
+    assert abs(J.var() - 1) < 4 * np.sqrt(2 / n)
+    assert abs(np.mean(J ** 4) - 3) < 4 * np.sqrt(96 / n)
+    Jm = J.reshape(-1, 3)
+    for a, b in ((0, 1), (0, 2), (1, 2)):
+        assert abs(np.corrcoef(Jm[:, a], Jm[:, b])[0, 1]) < 4 / np.sqrt(len(Jm))
+    assert np.array_equal(J, orc.gaussian_couplings(L, seed=4, sample=7))
+    assert not np.allclose(J, orc.gaussian_couplings(L, seed=4, sample=8))
