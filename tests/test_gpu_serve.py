@@ -1,0 +1,47 @@
+"""The continuous-batching request loop (needs a CUDA GPU): every result is
+the same alone and in the mix; requests wait for memory and are admitted in
+arrival order."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1006_2566_gb300 import serve  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def hsg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1006_2566_gb300 import build
+
+    build.build()
+    from paper_1006_2566_gb300 import hsg as h
+
+    return h
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(hsg):
+    reqs = serve.poisson_trace(14, rate_per_s=300.0, seed=8, sides=(8, 12, 16, 20, 24), sweep_range=(4, 30))
+    kw = dict(kind=hsg.HSG_METROPOLIS, hits=4, proposal=hsg.HSG_PROP_BALL, step=0.5, n_or=2, renorm_every=10)
+    budget = 3 * 28 * 24 ** 3  # room for three of the largest lattices: later arrivals must wait
+    res, st = serve.serve(reqs, kw, budget, 6, torch.cuda.Stream(), tick_sweeps=4, keep_spins=True, autotune=False)
+    assert st.completed == len(reqs)
+    assert st.max_batch >= 2  # requests overlapped on the device
+    by_id = {r.rid: r for r in res}
+    admitted = [by_id[q.rid].admitted for q in sorted(reqs, key=lambda q: q.arrival)]
+    assert all(a <= b for a, b in zip(admitted, admitted[1:]))  # arrival order
+    for q in reqs:
+        r = by_id[q.rid]
+        assert r.arrival <= r.admitted + 1e-9 <= r.finished + 1e-9
+        with hsg.Lattice(q.L, q.seed, q.sample, 0) as lat:
+            lat.generate_couplings()
+            lat.sweep(hsg.schedule(T=q.T, **kw), q.sweeps)
+            assert np.array_equal(r.spins, lat.spins()), q
+            assert abs(r.energy - lat.energy()) <= 2e-6
+    fifo, fst = serve.serve_fifo(reqs, kw, keep_spins=True)
+    assert fst.completed == len(reqs)
+    for f in fifo:
+        assert np.array_equal(f.spins, by_id[f.rid].spins)
+        assert abs(f.energy - by_id[f.rid].energy) <= 2e-6
