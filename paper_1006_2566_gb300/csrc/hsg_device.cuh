@@ -67,9 +67,24 @@ __device__ __forceinline__ float3 update_or(float3 s, float3 h) {
   return make_float3(fmaf(f, h.x, -s.x), fmaf(f, h.y, -s.y), fmaf(f, h.z, -s.z));
 }
 
+// The same sphere point with the fast sine/cosine (absolute error ~4e-7) on
+// the angle 2 pi u1 - pi and a reciprocal-square-root radius (2 ulp).
+__device__ __forceinline__ float3 sphere_point_fast(float u0, float u1) {
+  const float z = fmaf(2.0f, u0, -1.0f);
+  const float t = u0 * (1.0f - u0);  // > 0: u0 is strictly inside (0,1)
+  const float rho = 2.0f * t * rsqrtf(t);
+  float s, c;
+  __sincosf(6.283185307179586f * (u1 - 0.5f), &s, &c);
+  return make_float3(-rho * c, -rho * s, z);
+}
+
 // Multi-hit Metropolis at fixed field h.  Hit j uses the Philox draw at
 // counter (site, sweep_lo, MET<<24 | colour<<16 | j, sweep_hi).  The site
 // energy in the field is -s.h, dE = -(s' - s).h, accept iff u3 < exp(-beta dE).
+// The proposal uses the fast sphere point, the ball radius cbrt(u2) is
+// __powf(u2, 1/3) (relative error ~1e-6 for u2 in (0,1)), the normalisation
+// rsqrtf; the acceptance uses __expf, whose ~1e-6 relative error can only
+// flip decisions lying within ~1e-6 of their threshold.
 template <bool BALL>
 __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t site, uint32_t colour,
                                                     uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
@@ -78,20 +93,20 @@ __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t
     const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_MET << 24) | (colour << 16) | (uint32_t)j,
                                              sweep_hi),
                                   k0, k1);
-    const float3 d = sphere_point(u01(r.x), u01(r.y));
+    const float3 d = sphere_point_fast(u01(r.x), u01(r.y));
     float3 p;
     if (BALL) {
-      const float a = step * cbrtf(u01(r.z));
+      const float a = step * __powf(u01(r.z), 0.333333343f);
       const float3 v = make_float3(fmaf(a, d.x, s.x), fmaf(a, d.y, s.y), fmaf(a, d.z, s.z));
       const float n2 = dot3(v, v);
       if (n2 == 0.0f) continue;  // no direction: rejected
-      const float inv = 1.0f / sqrtf(n2);
+      const float inv = rsqrtf(n2);
       p = make_float3(v.x * inv, v.y * inv, v.z * inv);
     } else {
       p = d;
     }
     const float de = -dot3(make_float3(p.x - s.x, p.y - s.y, p.z - s.z), h);
-    if (u01(r.w) < expf(-beta * de)) s = p;
+    if (u01(r.w) < __expf(-beta * de)) s = p;
   }
   return s;
 }
