@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <string>
 #include <vector>
 
@@ -20,13 +21,17 @@ namespace {
 constexpr int kVersion = 100;  // 0.1.0
 constexpr int kMaxL = 1624;    // L^3 < 2^32: site indices are 32-bit Philox counters
 constexpr int kElogInit = 64;
+constexpr long long kMaxGraphPeriod = 64;  // longest sweep period captured as one graph
 
 thread_local std::string g_thread_error;
 int g_fail_alloc_countdown = 0;  // test hook: k-th allocation from now fails
 
+// A run of consecutive launches of one kernel class, bracketed by one pair
+// of events (count = launches in the run).
 struct ProfRec {
   int kclass;
   cudaEvent_t start, stop;
+  uint32_t count;
 };
 
 }  // namespace
@@ -50,9 +55,20 @@ struct hsg_ctx {
   int elog_cap = 0, elog_n = 0;
   double* host_e = nullptr;  // pinned, 1 double
   bool prof = false;
+  bool group = false;     // inside hsg_sweep: one event pair per run of same-class launches
+  bool run_open = false;  // recs.back() still lacks its stop event
   std::vector<ProfRec> recs;
   std::vector<cudaEvent_t> free_events;
   uint64_t launches = 0;
+  // Device counters: [0] the sweep counter the kernels read, [1] the energy
+  // log position; the host mirrors both (sweep, elog_n).
+  unsigned long long* d_ctr = nullptr;
+  // One captured period of sweeps (see hsg_sweep), replayed while the
+  // schedule, the kernel variant and the energy log buffer stay the same.
+  cudaGraphExec_t gexec = nullptr;
+  hsg_schedule gsched{};
+  int gvariant = 0, gperiod = 0, glaunches = 0;
+  double* gelog = nullptr;
   std::string err;
 };
 
@@ -93,30 +109,51 @@ cudaEvent_t take_event(hsg_ctx* c) {
   return e;
 }
 
-// Run `fn` (which launches `n_kernels` kernels on the context stream),
-// bracketed by profiler events when profiling is on.
+// Record the stop event of the open profiler run, if any.
+void close_run(hsg_ctx* c) {
+  if (!c->run_open) return;
+  cudaEvent_t b = take_event(c);
+  if (b) cudaEventRecord(b, c->stream);
+  c->recs.back().stop = b;
+  c->run_open = false;
+}
+
+// Run `fn` (which launches `n_kernels` kernels on the context stream).  With
+// the profiler on, each launch is bracketed by CUDA events on the stream;
+// inside hsg_sweep consecutive launches of one class share one bracket, so
+// that the events perturb the sweep as little as possible.
 template <typename F>
 hsg_status launch(hsg_ctx* c, int kclass, int n_kernels, const char* what, F&& fn) {
-  cudaEvent_t a = nullptr, b = nullptr;
-  if (c->prof) {
-    a = take_event(c);
-    b = take_event(c);
-    if (!a || !b) return fail(c, HSG_ECUDA, "cudaEventCreate failed");
+  if (c->prof && !(c->group && c->run_open && c->recs.back().kclass == kclass)) {
+    close_run(c);
+    cudaEvent_t a = take_event(c);
+    if (!a) return fail(c, HSG_ECUDA, "cudaEventCreate failed");
     cudaEventRecord(a, c->stream);
+    c->recs.push_back(ProfRec{kclass, a, nullptr, 0});
+    c->run_open = true;
   }
   cudaError_t e = fn();
   if (e != cudaSuccess) {
-    if (a) c->free_events.push_back(a);
-    if (b) c->free_events.push_back(b);
+    close_run(c);
     return cuda_fail(c, e, what);
   }
   c->launches += (uint64_t)n_kernels;
   if (c->prof) {
-    cudaEventRecord(b, c->stream);
-    c->recs.push_back(ProfRec{kclass, a, b});
+    c->recs.back().count += 1;
+    if (!c->group) close_run(c);
   }
   return HSG_OK;
 }
+
+// Inside hsg_sweep: group same-class launches; the run closes on exit.
+struct SweepGroup {
+  hsg_ctx* c;
+  explicit SweepGroup(hsg_ctx* ctx) : c(ctx) { c->group = true; }
+  ~SweepGroup() {
+    close_run(c);
+    c->group = false;
+  }
+};
 
 hsg_status ensure_stage(hsg_ctx* c, size_t bytes) {
   if (c->stage_bytes >= bytes) return HSG_OK;
@@ -138,11 +175,13 @@ void release(hsg_ctx* c) {
   dev_free(c->partials, s);
   dev_free(c->e_out, s);
   dev_free(c->elog, s);
+  dev_free(c->d_ctr, s);
   cudaStreamSynchronize(s);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
   if (c->host_e) cudaFreeHost(c->host_e);
   for (auto& r : c->recs) {
     cudaEventDestroy(r.start);
-    cudaEventDestroy(r.stop);
+    if (r.stop) cudaEventDestroy(r.stop);
   }
   for (auto e : c->free_events) cudaEventDestroy(e);
   delete c;
@@ -169,6 +208,7 @@ hsg::SweepArgs sweep_args(hsg_ctx* c, int colour, float beta, float step, int hi
   a.sweep_hi = (uint32_t)(c->sweep >> 32);
   a.beta = beta;
   a.step = step;
+  a.sweep_ptr = c->d_ctr;  // the device counter equals c->sweep in stream order
   return a;
 }
 
@@ -213,14 +253,83 @@ hsg_status run_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int col
   return launch(c, kclass, 1, "half-sweep kernel", [&] { return hsg::launch_half_sweep(upd, variant, a, c->stream); });
 }
 
-hsg_status run_energy(hsg_ctx* c, double* out_dev) {
+// E/N into *out_dev, or (logged) into the energy log at the device position.
+hsg_status run_energy(hsg_ctx* c, double* out_dev, bool logged) {
+  unsigned long long* idx = logged ? c->d_ctr + 1 : nullptr;
   return launch(c, HSG_PROF_ENERGY, 2, "energy kernels",
-                [&] { return hsg::launch_energy(c->spins, c->J, c->L, c->partials, out_dev, c->stream); });
+                [&] { return hsg::launch_energy(c->spins, c->J, c->L, c->partials, out_dev, idx, c->stream); });
+}
+
+hsg_status run_advance(hsg_ctx* c) {
+  return launch(c, HSG_PROF_LAYOUT, 1, "counter kernel", [&] { return hsg::launch_add_u64(c->d_ctr, 1, c->stream); });
 }
 
 hsg_status run_renorm(hsg_ctx* c) {
   return launch(c, HSG_PROF_RENORM, 1, "renorm kernel",
                 [&] { return hsg::launch_renorm(c->spins, c->N, c->sm_count, c->stream); });
+}
+
+// One sweep's launches in schedule order; the host mirrors of the sweep
+// counter and the energy-log position advance as the device ones will.
+hsg_status enqueue_one_sweep(hsg_ctx* c, const hsg_schedule* s) {
+  hsg_status st;
+  if (s->kind != HSG_NONE)
+    for (int colour = 0; colour < 2; ++colour)
+      if ((st = run_half_sweep(c, s, s->kind, colour)) != HSG_OK) return st;
+  for (int o = 0; o < s->n_or; ++o)
+    for (int colour = 0; colour < 2; ++colour)
+      if ((st = run_half_sweep(c, s, HSG_OVERRELAX, colour)) != HSG_OK) return st;
+  if ((st = run_advance(c)) != HSG_OK) return st;
+  c->sweep += 1;
+  if (s->renorm_every > 0 && c->sweep % (uint64_t)s->renorm_every == 0)
+    if ((st = run_renorm(c)) != HSG_OK) return st;
+  if (s->energy_every > 0 && c->sweep % (uint64_t)s->energy_every == 0) {
+    if ((st = run_energy(c, c->elog, true)) != HSG_OK) return st;
+    c->elog_n += 1;
+  }
+  return HSG_OK;
+}
+
+bool same_schedule(const hsg_schedule& a, const hsg_schedule& b) {
+  return a.kind == b.kind && a.hits == b.hits && a.proposal == b.proposal && a.step == b.step && a.n_or == b.n_or &&
+         a.T == b.T && a.renorm_every == b.renorm_every && a.energy_every == b.energy_every && a.kernel == b.kernel;
+}
+
+bool graph_matches(const hsg_ctx* c, const hsg_schedule* s, int variant, int period) {
+  return c->gexec && same_schedule(c->gsched, *s) && c->gvariant == variant && c->gperiod == period &&
+         c->gelog == c->elog;
+}
+
+// Capture `period` sweeps starting at the current counter (a multiple of
+// the period) into c->gexec.  Capturing runs nothing, so the host mirrors
+// are restored afterwards.
+hsg_status capture_period(hsg_ctx* c, const hsg_schedule* s, int variant, int period) {
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  c->gexec = nullptr;
+  const uint64_t sweep0 = c->sweep, launches0 = c->launches;
+  const int elog0 = c->elog_n;
+  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(c, e, "sweep capture");
+  hsg_status st = HSG_OK;
+  for (int j = 0; j < period && st == HSG_OK; ++j) st = enqueue_one_sweep(c, s);
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(c->stream, &g);
+  c->glaunches = (int)(c->launches - launches0);
+  c->launches = launches0;
+  c->sweep = sweep0;
+  c->elog_n = elog0;
+  if (st == HSG_OK && e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (st != HSG_OK) return st;
+  if (e != cudaSuccess) {
+    c->gexec = nullptr;
+    return cuda_fail(c, e, "sweep graph");
+  }
+  c->gsched = *s;
+  c->gvariant = variant;
+  c->gperiod = period;
+  c->gelog = c->elog;
+  return HSG_OK;
 }
 
 hsg_status grow_elog(hsg_ctx* c, int need) {
@@ -284,6 +393,7 @@ hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint
       {reinterpret_cast<void**>(&c->J), sizeof(float) * 3 * (size_t)c->N, "couplings"},
       {reinterpret_cast<void**>(&c->partials), sizeof(double) * hsg::energy_partials(L), "energy partials"},
       {reinterpret_cast<void**>(&c->e_out), sizeof(double), "energy result"},
+      {reinterpret_cast<void**>(&c->d_ctr), 2 * sizeof(unsigned long long), "device counters"},
   };
   for (auto& a : allocs) {
     e = dev_alloc(a.p, a.bytes, c->stream);
@@ -300,9 +410,10 @@ hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint
     return st;
   }
   e = cudaMallocHost(&c->host_e, sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) {
-    c->host_e = nullptr;
-    st = cuda_fail(nullptr, e, "pinned host slot");
+    if (!c->host_e) c->host_e = nullptr;
+    st = cuda_fail(nullptr, e, "pinned host slot / counters");
     release(c);
     return st;
   }
@@ -394,20 +505,32 @@ hsg_status hsg_sweep(hsg_ctx* c, const hsg_schedule* s, int n_sweeps) {
     st = grow_elog(c, c->elog_n + (int)logged);
     if (st != HSG_OK) return st;
   }
-  for (int k = 0; k < n_sweeps; ++k) {
-    if (s->kind != HSG_NONE) {
-      for (int colour = 0; colour < 2; ++colour)
-        if ((st = run_half_sweep(c, s, s->kind, colour)) != HSG_OK) return st;
-    }
-    for (int o = 0; o < s->n_or; ++o)
-      for (int colour = 0; colour < 2; ++colour)
-        if ((st = run_half_sweep(c, s, HSG_OVERRELAX, colour)) != HSG_OK) return st;
-    c->sweep += 1;
-    if (s->renorm_every > 0 && c->sweep % (uint64_t)s->renorm_every == 0)
-      if ((st = run_renorm(c)) != HSG_OK) return st;
-    if (s->energy_every > 0 && c->sweep % (uint64_t)s->energy_every == 0) {
-      if ((st = run_energy(c, c->elog + c->elog_n)) != HSG_OK) return st;
-      c->elog_n += 1;
+  SweepGroup group_guard(c);
+  // Sweeps run in periods of P = lcm(renorm_every, energy_every) sweeps
+  // (1 without cadences).  On a non-default stream and without the
+  // profiler, a period that starts at a multiple of P is captured once as a
+  // CUDA graph (the kernels read the sweep counter and the energy-log
+  // position from device memory) and replayed; other sweeps are launched
+  // directly.  Both paths issue the same kernels in the same order.
+  const int variant = pick_variant(c, s->kernel);
+  long long period = 1;
+  if (s->renorm_every > 0) period = std::lcm(period, (long long)s->renorm_every);
+  if (s->energy_every > 0) period = std::lcm(period, (long long)s->energy_every);
+  const bool graphs = c->stream != nullptr && !c->prof && period <= kMaxGraphPeriod;
+  int k = 0;
+  while (k < n_sweeps) {
+    if (graphs && c->sweep % (uint64_t)period == 0 && n_sweeps - k >= period) {
+      if (!graph_matches(c, s, variant, (int)period) && (st = capture_period(c, s, variant, (int)period)) != HSG_OK)
+        return st;
+      cudaError_t e = cudaGraphLaunch(c->gexec, c->stream);
+      if (e != cudaSuccess) return cuda_fail(c, e, "sweep graph launch");
+      c->launches += (uint64_t)c->glaunches;
+      c->sweep += (uint64_t)period;
+      if (s->energy_every > 0) c->elog_n += (int)(period / s->energy_every);
+      k += (int)period;
+    } else {
+      if ((st = enqueue_one_sweep(c, s)) != HSG_OK) return st;
+      k += 1;
     }
   }
   return HSG_OK;
@@ -417,7 +540,7 @@ hsg_status hsg_energy(hsg_ctx* c, double* e_per_spin) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
   if (!e_per_spin) return fail(c, HSG_EINVAL, "e_per_spin is NULL");
   if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
-  hsg_status st = run_energy(c, c->e_out);
+  hsg_status st = run_energy(c, c->e_out, false);
   if (st != HSG_OK) return st;
   cudaError_t e = cudaMemcpyAsync(c->host_e, c->e_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -440,6 +563,9 @@ hsg_status hsg_get_energy_log(hsg_ctx* c, double* out, int max_n, int* n) {
 
 hsg_status hsg_clear_energy_log(hsg_ctx* c) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "counter kernel",
+                         [&] { return hsg::launch_set_u64(c->d_ctr + 1, 0, c->stream); });
+  if (st != HSG_OK) return st;
   c->elog_n = 0;
   return HSG_OK;
 }
@@ -498,6 +624,9 @@ hsg_status hsg_get_sweep(hsg_ctx* c, uint64_t* sweep) {
 
 hsg_status hsg_set_sweep(hsg_ctx* c, uint64_t sweep) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "counter kernel",
+                         [&] { return hsg::launch_set_u64(c->d_ctr, sweep, c->stream); });
+  if (st != HSG_OK) return st;
   c->sweep = sweep;
   return HSG_OK;
 }
@@ -520,6 +649,7 @@ hsg_status hsg_renorm(hsg_ctx* c) {
 
 hsg_status hsg_profile(hsg_ctx* c, int on) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (!on) close_run(c);
   c->prof = on != 0;
   return HSG_OK;
 }
@@ -527,17 +657,18 @@ hsg_status hsg_profile(hsg_ctx* c, int on) {
 hsg_status hsg_profile_read(hsg_ctx* c, int kclass, double* total_ms, uint64_t* launches) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
   if (kclass < 0 || kclass >= HSG_PROF_COUNT) return fail(c, HSG_EINVAL, "bad kernel class");
+  close_run(c);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
   double ms = 0.0;
   uint64_t n = 0;
   for (const auto& r : c->recs) {
-    if (r.kclass != kclass) continue;
+    if (r.kclass != kclass || !r.stop) continue;
     float t = 0.0f;
     e = cudaEventElapsedTime(&t, r.start, r.stop);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
     ms += t;
-    n += 1;
+    n += r.count;
   }
   if (total_ms) *total_ms = ms;
   if (launches) *launches = n;
@@ -548,9 +679,10 @@ hsg_status hsg_profile_reset(hsg_ctx* c) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
+  close_run(c);
   for (auto& r : c->recs) {
     c->free_events.push_back(r.start);
-    c->free_events.push_back(r.stop);
+    if (r.stop) c->free_events.push_back(r.stop);
   }
   c->recs.clear();
   return HSG_OK;

@@ -163,9 +163,11 @@ __global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const float4*
 }
 
 // Energy, second pass: one block adds the partials in a fixed order and
-// writes E/N = -(sum)/N.
+// writes E/N = -(sum)/N to *out, or, with log_idx set, to out[*log_idx]
+// and then advances *log_idx.
 __global__ void __launch_bounds__(FINAL_THREADS) k_energy_final(const double* __restrict__ partials, int n,
-                                                                double inv_n_sites, double* __restrict__ out) {
+                                                                double inv_n_sites, double* __restrict__ out,
+                                                                unsigned long long* __restrict__ log_idx) {
   double v = 0.0;
   for (int k = threadIdx.x; k < n; k += FINAL_THREADS) v += partials[k];
   __shared__ double warp_part[FINAL_THREADS / 32];
@@ -175,9 +177,20 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_energy_final(const double* __
   if (threadIdx.x < 32) {
     double w = warp_part[threadIdx.x];
     w = warp_sum(w);
-    if (threadIdx.x == 0) *out = -w * inv_n_sites;
+    if (threadIdx.x == 0) {
+      if (log_idx) {
+        const unsigned long long k = *log_idx;
+        out[k] = -w * inv_n_sites;
+        *log_idx = k + 1;
+      } else {
+        *out = -w * inv_n_sites;
+      }
+    }
   }
 }
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+__global__ void k_add_u64(unsigned long long* p, unsigned long long d) { *p += d; }
 
 // Renormalisation of every spin (renorm_spin, hsg_device.cuh).
 __global__ void k_renorm(float4* __restrict__ S, long long n) {
@@ -233,12 +246,23 @@ size_t energy_partials(int L) {
   return (size_t)(b < ENERGY_BLOCKS ? b : ENERGY_BLOCKS);
 }
 
-cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out, cudaStream_t s) {
+cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out,
+                          unsigned long long* log_idx, cudaStream_t s) {
   const int nb = (int)energy_partials(L);
   k_energy_partial<<<nb, ENERGY_THREADS, 0, s>>>(S, J, L, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_energy_final<<<1, FINAL_THREADS, 0, s>>>(partials, nb, 1.0 / ((double)L * L * L), out);
+  k_energy_final<<<1, FINAL_THREADS, 0, s>>>(partials, nb, 1.0 / ((double)L * L * L), out, log_idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t s) {
+  k_set_u64<<<1, 1, 0, s>>>(p, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_u64(unsigned long long* p, unsigned long long d, cudaStream_t s) {
+  k_add_u64<<<1, 1, 0, s>>>(p, d);
   return cudaGetLastError();
 }
 

@@ -23,6 +23,9 @@ struct SweepArgs {
   int L, Lh, colour, hits;
   uint32_t k0, k1, sweep_lo, sweep_hi;
   float beta, step;
+  // When set, the sweep counter is read from this device word instead of
+  // sweep_lo/sweep_hi (so that a captured graph can be replayed).
+  const unsigned long long* sweep_ptr;
 };
 
 // Kernel variants (values match HSG_KERNEL_*).
@@ -49,8 +52,15 @@ cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t
 
 // Energy: number of FP64 partial sums the first pass writes, and the
 // two-pass E/N into *out (device).  Two launches.
+// With log_idx set, E/N goes to out[*log_idx] and *log_idx is incremented
+// (an energy log whose position lives in device memory).
 size_t energy_partials(int L);
-cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out, cudaStream_t s);
+cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out,
+                          unsigned long long* log_idx, cudaStream_t s);
+
+// Device counters: *p = v, *p += d.  One single-thread launch each.
+cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t s);
+cudaError_t launch_add_u64(unsigned long long* p, unsigned long long d, cudaStream_t s);
 
 // FP64 renormalisation of n float4 spins.  One launch.
 cudaError_t launch_renorm(float4* S, long long n, int sm_count, cudaStream_t s);

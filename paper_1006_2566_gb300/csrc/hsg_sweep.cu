@@ -30,16 +30,28 @@ __device__ __forceinline__ uint32_t site_index(int xh, int p, int y, int z, int 
 // ---------------------------------------------------------------------------
 constexpr int G_THREADS = 128;
 
-// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.
+// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.  The over-relaxation and
+// heat-bath kernels are held to 32 registers so that 16 blocks (full
+// occupancy) fit on an SM (measured at L = 256: OR 92 us at 32 registers vs
+// 99 us at 36-40); Metropolis, which would spill, keeps its registers.
 template <int U>
-__global__ void __launch_bounds__(G_THREADS) k_half_sweep_global(const SweepArgs a) {
+__global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
+    k_half_sweep_global(const SweepArgs a) {
   const uint32_t xh = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t z = blockIdx.z;
   const uint32_t L = a.L, Lh = a.Lh;
   if (xh >= Lh || y >= L) return;
+  uint32_t sweep_lo = a.sweep_lo, sweep_hi = a.sweep_hi;
+  if constexpr (U != U_OR) {
+    if (a.sweep_ptr) {
+      const unsigned long long sw = *a.sweep_ptr;
+      sweep_lo = (uint32_t)sw;
+      sweep_hi = (uint32_t)(sw >> 32);
+    }
+  }
   half_sweep_site<U>(a.own, a.oth, a.jx_own, a.jy_own, a.jz_own, a.jx_oth, a.jy_oth, a.jz_oth, xh, y, z, L, Lh,
-                     (uint32_t)a.colour, a.sweep_lo, a.sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
+                     (uint32_t)a.colour, sweep_lo, sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
 }
 
 // ---------------------------------------------------------------------------
@@ -64,6 +76,14 @@ __global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
   const int y_top = (y0 + L - 1) % L, y_bot = (y0 + TY) % L;
   const long long plane_sz = (long long)L * Lh;
   const long long col = (long long)yw * Lh + xw;  // this slot's offset in a plane
+  uint32_t sweep_lo = a.sweep_lo, sweep_hi = a.sweep_hi;
+  if constexpr (U != U_OR) {
+    if (a.sweep_ptr) {
+      const unsigned long long sw = *a.sweep_ptr;
+      sweep_lo = (uint32_t)sw;
+      sweep_hi = (uint32_t)(sw >> 32);
+    }
+  }
 
   int zprev = wrap_dec(z0, L);
   float4 s_zm = __ldg(a.oth + zprev * plane_sz + col);
@@ -96,8 +116,8 @@ __global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
       }
       const float3 h = local_field(buf[ty + 1][tx + 1 + p], buf[ty + 1][tx + p], buf[ty + 2][tx + 1],
                                    buf[ty][tx + 1], s_zp, s_zm, jxp, jxm, jyp, jym, jzp, jzm);
-      const float3 t = update_site<U>(s, h, site_index(xh, p, y, z, L), (uint32_t)a.colour, a.sweep_lo,
-                                      a.sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
+      const float3 t = update_site<U>(s, h, site_index(xh, p, y, z, L), (uint32_t)a.colour, sweep_lo, sweep_hi,
+                                      a.k0, a.k1, a.beta, a.step, a.hits);
       a.own[q] = make_float4(t.x, t.y, t.z, 0.0f);
       jzm = jz_here;
     }

@@ -427,6 +427,37 @@ def test_long_run_energy_statistics_match_oracle(hsg):
     assert abs(mg - mr) < 3 * math.hypot(eg, er) + 1e-6, (mg, eg, mr, er)
 
 
+@pytest.mark.parametrize("kind", ["HB", "MET"])
+def test_graph_replayed_sweeps_equal_direct_launches(hsg, kind):
+    """On a non-default stream hsg_sweep replays captured periods of
+    lcm(renorm_every, energy_every) sweeps; on the default stream it
+    launches every kernel directly.  Spins, energy log, counters and the
+    launch count must agree, including a call that starts mid-period, a
+    counter set by hand and a cleared log."""
+    L = 16
+    J = inputs.gaussian_couplings(L, seed=23)
+    k = hsg.HSG_HEATBATH if kind == "HB" else hsg.HSG_METROPOLIS
+    sched = hsg.schedule(kind=k, hits=2, proposal=1, T=0.6, n_or=2, renorm_every=5, energy_every=2)
+    outs = []
+    for stream in (torch.cuda.Stream(), None):
+        with hsg.Lattice(L, 23, stream=stream) as lat:
+            lat.set_couplings(J)
+            n0 = hsg.hsg_launch_count(lat.ctx)
+            lat.sweep(sched, 3)  # not a whole period: direct launches
+            lat.sweep_count = 10  # jump to a period boundary
+            lat.sweep(sched, 25)  # two replayed periods + 5 direct sweeps
+            log1 = lat.energy_log()
+            hsg.hsg_clear_energy_log(lat.ctx)
+            lat.sweep(sched, 10)
+            outs.append((lat.spins(), log1, lat.energy_log(), lat.sweep_count, hsg.hsg_launch_count(lat.ctx) - n0))
+    a, b = outs
+    assert np.array_equal(a[0], b[0])
+    assert np.array_equal(a[1], b[1]) and len(a[1]) == 1 + 12
+    assert np.array_equal(a[2], b[2]) and len(a[2]) == 5
+    assert a[3] == b[3] == 45
+    assert a[4] == b[4]
+
+
 def test_checkpoint_resume_is_bit_identical(hsg):
     L = 24
     J = inputs.gaussian_couplings(L, seed=5)
@@ -497,6 +528,7 @@ def test_profiler_counts_launches(hsg):
         assert counts[hsg.HSG_PROF_OVERRELAX] == 80
         assert counts[hsg.HSG_PROF_ENERGY] == 2 and counts[hsg.HSG_PROF_RENORM] == 2
         assert ms > 0
-        assert hsg.hsg_launch_count(lat.ctx) - n0 == 20 + 80 + 2 * 2 + 2
+        # 20 heat-bath + 80 OR half-sweeps, 10 counter advances, 2 energies (2 kernels), 2 renorms
+        assert hsg.hsg_launch_count(lat.ctx) - n0 == 20 + 80 + 10 + 2 * 2 + 2
         hsg.hsg_profile_reset(lat.ctx)
         assert hsg.hsg_profile_read(lat.ctx, hsg.HSG_PROF_OVERRELAX)[1] == 0
