@@ -57,6 +57,11 @@ WORKLOADS = {
         energy_every=10, sweeps_per_step=10,
         desc=("L=16 periodic 3D Heisenberg spin glass, 1 sample, Gaussian J; checkerboard Metropolis 1 hit, "
               "uniform-sphere proposal, T=1.0; E/N every 10 sweeps; 1 step = 10 sweeps")),
+    "l128_metor_fused": dict(
+        L=128, seed=2, kind="METOR", T=0.5, n_or=0, hits=4, proposal="BALL", step=0.5, renorm_every=10,
+        energy_every=10, sweeps_per_step=10,
+        desc=("L=128, 1 sample, fp32; per sweep the fused colour pass (4-hit Metropolis, ball 0.5, T=0.5, then one "
+              "over-relaxation reflection about the same field; opt-in chain); 1 step = 10 sweeps")),
     "l128_met_or": dict(
         L=128, seed=2, kind="MET", T=0.5, n_or=1, hits=4, proposal="BALL", step=0.5, renorm_every=10,
         energy_every=10, sweeps_per_step=10,
@@ -195,13 +200,13 @@ def profiled_traffic(kernel_variant: str, L: int):
 
 def step_units(wl) -> int:
     """Site updates in one step (one per site per main-update or OR pass)."""
-    passes = (1 if wl["kind"] in ("HB", "MET") else 0) + wl["n_or"]
+    passes = {"HB": 1, "MET": 1, "METOR": 2}.get(wl["kind"], 0) + wl["n_or"]
     return (wl["L"] ** 3) * passes * wl["sweeps_per_step"]
 
 
 def step_bytes(wl) -> int:
     n = wl["L"] ** 3
-    main = {"HB": BYTES_HB, "MET": BYTES_OR}.get(wl["kind"], 0)
+    main = {"HB": BYTES_HB, "MET": BYTES_OR, "METOR": BYTES_OR}.get(wl["kind"], 0)
     per_sweep = n * (main + wl["n_or"] * BYTES_OR)
     s = wl["sweeps_per_step"]
     extra = 0
@@ -236,7 +241,8 @@ def run_ours(args, wl):
 
     L = wl["L"]
     N = L ** 3
-    kind = {"HB": hsg.HSG_HEATBATH, "MET": hsg.HSG_METROPOLIS, "NONE": hsg.HSG_NONE}[wl["kind"]]
+    kind = {"HB": hsg.HSG_HEATBATH, "MET": hsg.HSG_METROPOLIS, "METOR": hsg.HSG_METROPOLIS_OR,
+            "NONE": hsg.HSG_NONE}[wl["kind"]]
     proposal = {"SPHERE": hsg.HSG_PROP_SPHERE, "BALL": hsg.HSG_PROP_BALL}[wl["proposal"]]
     kernel = {"auto": hsg.HSG_KERNEL_AUTO, "global": hsg.HSG_KERNEL_GLOBAL, "slab": hsg.HSG_KERNEL_SLAB}[args.kernel]
     sched = hsg.schedule(kind=kind, hits=wl["hits"], proposal=proposal, step=wl["step"], n_or=wl["n_or"], T=wl["T"],
@@ -397,7 +403,7 @@ def _oracle_setup(wl):
     L = wl["L"]
     J = inputs.round_to_f32(inputs.gaussian_couplings(L, seed=wl["seed"], dtype=np.float32))
     s = oracle.init_spins(L, wl["seed"])
-    kind = {"HB": oracle.HB, "MET": oracle.MET}.get(wl["kind"], -1)
+    kind = {"HB": oracle.HB, "MET": oracle.MET, "METOR": oracle.MET_OR}.get(wl["kind"], -1)
     p = oracle.Params(key=oracle.key(wl["seed"]), sweep=0, beta=1.0 / wl["T"], step=wl["step"], hits=wl["hits"],
                       proposal=oracle.PROP_BALL if wl["proposal"] == "BALL" else oracle.PROP_SPHERE)
     return oracle, L, J, s, kind, p
@@ -410,7 +416,7 @@ def _oracle_sample_sweep(oracle, L, J, s, kind, p, i0, i1):
     if kind >= 0:
         for c in (0, 1):
             oracle.half_sweep_range(L, J, s, kind, c, p, i0, i1)
-        n += i1 - i0
+        n += (i1 - i0) * (2 if kind == oracle.MET_OR else 1)
     return n
 
 

@@ -52,7 +52,13 @@ enum {
   HSG_NONE = 0,
   HSG_METROPOLIS = 1, /* multi-hit Metropolis (named in Sec. 2; Table 3) */
   HSG_HEATBATH = 2,   /* heat-bath (named in Sec. 2 and Sec. 4) */
-  HSG_OVERRELAX = 3   /* over-relaxation (Sec. 4); only for hsg_half_sweep */
+  HSG_OVERRELAX = 3,  /* over-relaxation (Sec. 4); only for hsg_half_sweep */
+  /* Fused colour pass (opt-in; not in the paper): at every site the
+   * Metropolis hits, then one over-relaxation reflection about the same
+   * local field -- within a colour's pass the neighbours do not move.  A
+   * different chain from Metropolis followed by OR sweeps, with the same
+   * equilibrium; it moves each spin twice per half-sweep of memory traffic. */
+  HSG_METROPOLIS_OR = 4
 };
 
 /* Metropolis proposals. */
@@ -104,7 +110,7 @@ enum {
  * in the Duff et al. (JCGT 2017) frame of h; uniform on S^2 if x < 1e-6).
  */
 typedef struct hsg_schedule {
-  int kind;         /* HSG_NONE | HSG_METROPOLIS | HSG_HEATBATH */
+  int kind;         /* HSG_NONE | HSG_METROPOLIS | HSG_HEATBATH | HSG_METROPOLIS_OR */
   int hits;         /* Metropolis hits per site per half-sweep, 1..65535 */
   int proposal;     /* HSG_PROP_SPHERE | HSG_PROP_BALL */
   float step;       /* ball-proposal scale, > 0 */

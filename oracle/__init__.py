@@ -21,7 +21,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hsg_oracle.c")
 _LIB = os.path.join(_HERE, "libhsg_oracle.so")
 
-OR, MET, HB = 0, 1, 2
+OR, MET, HB, MET_OR = 0, 1, 2, 3
 PROP_SPHERE, PROP_BALL = 0, 1
 KIND_INIT, KIND_JGEN, KIND_MET, KIND_HB = 1, 2, 3, 4
 

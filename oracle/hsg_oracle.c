@@ -46,8 +46,10 @@
 
 #define ORACLE_PI 3.14159265358979323846
 
-/* Update kinds and random-number stream kinds. */
-enum { ORACLE_OR = 0, ORACLE_MET = 1, ORACLE_HB = 2 };
+/* Update kinds and random-number stream kinds.  ORACLE_MET_OR is the fused
+ * colour pass: the Metropolis hits, then one over-relaxation reflection
+ * about the same local field (an opt-in schedule, not the paper's). */
+enum { ORACLE_OR = 0, ORACLE_MET = 1, ORACLE_HB = 2, ORACLE_MET_OR = 3 };
 enum { ORACLE_PROP_SPHERE = 0, ORACLE_PROP_BALL = 1 };
 enum { ORACLE_KIND_INIT = 1, ORACLE_KIND_JGEN = 2, ORACLE_KIND_MET = 3, ORACLE_KIND_HB = 4 };
 
@@ -63,7 +65,7 @@ typedef struct {
 
 /* A sweep schedule. */
 typedef struct {
-  int kind;          /* main update: -1 none, ORACLE_MET or ORACLE_HB */
+  int kind;          /* main update: -1 none, ORACLE_MET, ORACLE_HB or ORACLE_MET_OR */
   int hits;
   int proposal;
   double step;
@@ -345,6 +347,12 @@ void oracle_update_site(int upd, const double s[3], const double h[3], const ora
     update_or(s, h, out);
   } else if (upd == ORACLE_MET) {
     update_metropolis(s, h, p, site, colour, out, margin);
+  } else if (upd == ORACLE_MET_OR) {
+    /* The neighbours do not move during a colour's pass, so h is the same
+     * for the Metropolis hits and the reflection that follows them. */
+    double mid[3];
+    update_metropolis(s, h, p, site, colour, mid, margin);
+    update_or(mid, h, out);
   } else {
     update_heatbath(h, p, site, colour, out);
   }
@@ -402,7 +410,7 @@ void oracle_sweeps(int L, const double* J, double* s, const oracle_schedule* sch
   double n = (double)L * L * L;
   for (int k = 0; k < n_sweeps; ++k) {
     p.sweep = *sweep;
-    if (sch->kind == ORACLE_MET || sch->kind == ORACLE_HB) {
+    if (sch->kind == ORACLE_MET || sch->kind == ORACLE_HB || sch->kind == ORACLE_MET_OR) {
       oracle_half_sweep(L, J, s, sch->kind, 0, &p, NULL);
       oracle_half_sweep(L, J, s, sch->kind, 1, &p, NULL);
     }

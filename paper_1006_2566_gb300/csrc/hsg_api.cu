@@ -214,8 +214,9 @@ hsg::SweepArgs sweep_args(hsg_ctx* c, int colour, float beta, float step, int hi
 
 hsg_status check_schedule(hsg_ctx* c, const hsg_schedule* s, bool need_kind) {
   if (!s) return fail(c, HSG_EINVAL, "schedule is NULL");
-  if (need_kind && s->kind != HSG_NONE && s->kind != HSG_METROPOLIS && s->kind != HSG_HEATBATH)
-    return fail(c, HSG_EINVAL, "schedule.kind must be HSG_NONE, HSG_METROPOLIS or HSG_HEATBATH");
+  if (need_kind && s->kind != HSG_NONE && s->kind != HSG_METROPOLIS && s->kind != HSG_HEATBATH &&
+      s->kind != HSG_METROPOLIS_OR)
+    return fail(c, HSG_EINVAL, "schedule.kind must be HSG_NONE, HSG_METROPOLIS, HSG_HEATBATH or HSG_METROPOLIS_OR");
   if (s->hits < 1 || s->hits > 65535) return fail(c, HSG_EINVAL, "schedule.hits must be in [1, 65535]");
   if (s->proposal != HSG_PROP_SPHERE && s->proposal != HSG_PROP_BALL)
     return fail(c, HSG_EINVAL, "schedule.proposal must be HSG_PROP_SPHERE or HSG_PROP_BALL");
@@ -243,6 +244,9 @@ hsg_status run_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int col
     kclass = HSG_PROF_OVERRELAX;
   } else if (update == HSG_METROPOLIS) {
     upd = s->proposal == HSG_PROP_BALL ? hsg::U_MET_BALL : hsg::U_MET_SPHERE;
+    kclass = HSG_PROF_METROPOLIS;
+  } else if (update == HSG_METROPOLIS_OR) {
+    upd = s->proposal == HSG_PROP_BALL ? hsg::U_MET_OR_BALL : hsg::U_MET_OR_SPHERE;
     kclass = HSG_PROF_METROPOLIS;
   } else {
     upd = hsg::U_HB;
@@ -635,8 +639,8 @@ hsg_status hsg_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int col
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
   hsg_status st = check_schedule(c, s, false);
   if (st != HSG_OK) return st;
-  if (update != HSG_OVERRELAX && update != HSG_METROPOLIS && update != HSG_HEATBATH)
-    return fail(c, HSG_EINVAL, "update must be HSG_OVERRELAX, HSG_METROPOLIS or HSG_HEATBATH");
+  if (update != HSG_OVERRELAX && update != HSG_METROPOLIS && update != HSG_HEATBATH && update != HSG_METROPOLIS_OR)
+    return fail(c, HSG_EINVAL, "update must be HSG_OVERRELAX, HSG_METROPOLIS, HSG_HEATBATH or HSG_METROPOLIS_OR");
   if (colour != 0 && colour != 1) return fail(c, HSG_EINVAL, "colour must be 0 or 1");
   if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
   return run_half_sweep(c, s, update, colour);

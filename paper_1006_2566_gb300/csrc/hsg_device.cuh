@@ -18,8 +18,10 @@
 
 namespace hsg {
 
-// Update kinds of the half-sweep kernels.
-enum UpdKind : int { U_OR = 0, U_MET_SPHERE = 1, U_MET_BALL = 2, U_HB = 3 };
+// Update kinds of the half-sweep kernels.  U_MET_OR_* is the fused colour
+// pass: the Metropolis hits, then one over-relaxation reflection about the
+// same field.
+enum UpdKind : int { U_OR = 0, U_MET_SPHERE = 1, U_MET_BALL = 2, U_HB = 3, U_MET_OR_SPHERE = 4, U_MET_OR_BALL = 5 };
 
 // Philox stream kinds (third counter word, bits 24..31).
 constexpr uint32_t KIND_INIT = 1u, KIND_JGEN = 2u, KIND_MET = 3u, KIND_HB = 4u;
@@ -184,6 +186,10 @@ __device__ __forceinline__ float3 update_site(float3 s, float3 h, uint32_t site,
     return update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
   } else if constexpr (U == U_MET_BALL) {
     return update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  } else if constexpr (U == U_MET_OR_SPHERE) {
+    return update_or(update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits), h);
+  } else if constexpr (U == U_MET_OR_BALL) {
+    return update_or(update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits), h);
   } else {
     return update_heatbath(h, site, colour, sweep_lo, sweep_hi, k0, k1, beta);
   }

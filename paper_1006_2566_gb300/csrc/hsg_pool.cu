@@ -368,6 +368,8 @@ cudaError_t launch_pool_half(hsg_pool* p, int upd, uint32_t colour, float step, 
     case hsg::U_OR: k_pool_half_sweep<hsg::U_OR><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
     case hsg::U_MET_SPHERE: k_pool_half_sweep<hsg::U_MET_SPHERE><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
     case hsg::U_MET_BALL: k_pool_half_sweep<hsg::U_MET_BALL><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
+    case hsg::U_MET_OR_SPHERE: k_pool_half_sweep<hsg::U_MET_OR_SPHERE><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
+    case hsg::U_MET_OR_BALL: k_pool_half_sweep<hsg::U_MET_OR_BALL><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
     default: k_pool_half_sweep<hsg::U_HB><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
   }
   p->launches += 1;
@@ -379,8 +381,10 @@ cudaError_t launch_pool_half(hsg_pool* p, int upd, uint32_t colour, float step, 
 cudaError_t enqueue_sweep(hsg_pool* p, const hsg_schedule* s) {
   cudaError_t e = cudaSuccess;
   if (s->kind != HSG_NONE) {
-    const int upd = s->kind == HSG_HEATBATH ? hsg::U_HB
-                                            : (s->proposal == HSG_PROP_BALL ? hsg::U_MET_BALL : hsg::U_MET_SPHERE);
+    const bool ball = s->proposal == HSG_PROP_BALL;
+    const int upd = s->kind == HSG_HEATBATH        ? hsg::U_HB
+                    : s->kind == HSG_METROPOLIS_OR ? (ball ? hsg::U_MET_OR_BALL : hsg::U_MET_OR_SPHERE)
+                                                   : (ball ? hsg::U_MET_BALL : hsg::U_MET_SPHERE);
     for (uint32_t c = 0; c < 2 && e == cudaSuccess; ++c) e = launch_pool_half(p, upd, c, s->step, s->hits);
   }
   for (int o = 0; o < s->n_or && e == cudaSuccess; ++o)
@@ -401,8 +405,8 @@ cudaError_t enqueue_sweep(hsg_pool* p, const hsg_schedule* s) {
 
 hsg_status check_pool_schedule(hsg_pool* p, const hsg_schedule* s) {
   if (!s) return pfail(p, HSG_EINVAL, "schedule is NULL");
-  if (s->kind != HSG_NONE && s->kind != HSG_METROPOLIS && s->kind != HSG_HEATBATH)
-    return pfail(p, HSG_EINVAL, "schedule.kind must be HSG_NONE, HSG_METROPOLIS or HSG_HEATBATH");
+  if (s->kind != HSG_NONE && s->kind != HSG_METROPOLIS && s->kind != HSG_HEATBATH && s->kind != HSG_METROPOLIS_OR)
+    return pfail(p, HSG_EINVAL, "schedule.kind must be HSG_NONE, HSG_METROPOLIS, HSG_HEATBATH or HSG_METROPOLIS_OR");
   if (s->hits < 1 || s->hits > 65535) return pfail(p, HSG_EINVAL, "schedule.hits must be in [1, 65535]");
   if (s->proposal != HSG_PROP_SPHERE && s->proposal != HSG_PROP_BALL)
     return pfail(p, HSG_EINVAL, "schedule.proposal must be HSG_PROP_SPHERE or HSG_PROP_BALL");

@@ -147,6 +147,8 @@ cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, cudaStre
     case U_MET_SPHERE: return launch_kind<U_MET_SPHERE>(variant, a, s);
     case U_MET_BALL: return launch_kind<U_MET_BALL>(variant, a, s);
     case U_HB: return launch_kind<U_HB>(variant, a, s);
+    case U_MET_OR_SPHERE: return launch_kind<U_MET_OR_SPHERE>(variant, a, s);
+    case U_MET_OR_BALL: return launch_kind<U_MET_OR_BALL>(variant, a, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -19,7 +19,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhsg.so")
 
 HSG_OK, HSG_EINVAL, HSG_ENOMEM, HSG_ECUDA, HSG_ETIMEOUT, HSG_EBUSY = range(6)
-HSG_NONE, HSG_METROPOLIS, HSG_HEATBATH, HSG_OVERRELAX = range(4)
+HSG_NONE, HSG_METROPOLIS, HSG_HEATBATH, HSG_OVERRELAX, HSG_METROPOLIS_OR = range(5)
 HSG_PROP_SPHERE, HSG_PROP_BALL = 0, 1
 HSG_F32, HSG_F64 = 0, 1
 HSG_HOST, HSG_DEVICE = 0, 1

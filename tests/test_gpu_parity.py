@@ -229,6 +229,52 @@ def test_metropolis_half_sweep_parity(hsg, variant, case):
         assert moved[mask].mean() > 0.05  # the chain does move
 
 
+FUSED_CASES = [(16, 0, 1, 1.0), (24, 1, 4, 0.5), (40, 1, 2, 0.3)]
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("case", FUSED_CASES)
+def test_fused_metropolis_or_half_sweep_parity(hsg, variant, case):
+    """The opt-in fused colour pass (Metropolis hits, then one reflection
+    about the same field) against the oracle's MET_OR mode."""
+    L, proposal, hits, T = case
+    J, s32 = oracle_state(L, 910 + L, 920 + L)
+    Jr = inputs.round_to_f32(J)
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS_OR, hits=hits, proposal=proposal, step=0.5, T=T, kernel=variant)
+    for colour in (0, 1):
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_METROPOLIS_OR, colour, sched, seed=31, sweep=4)
+        before = s32.astype(np.float64)
+        ref = before.copy()
+        p = oracle.Params(key=oracle.key(31), sweep=4, beta=1.0 / T, step=0.5, hits=hits, proposal=proposal)
+        margins = oracle.half_sweep(L, Jr, ref, oracle.MET_OR, colour, p, want_margins=True)
+        near = colour_mask(L, colour) & (margins < TOL)
+        assert near.sum() <= max(2, 0.002 * colour_mask(L, colour).sum())
+        check_half_sweep(L, Jr, before, got, ref, colour, exclude=near)
+
+
+def test_fused_long_run_energy_statistics_match_oracle(hsg):
+    """L = 12, fused Metropolis (ball, 2 hits) + reflection at T = 0.7 for
+    1200 sweeps: mean E/N agrees with the oracle's within 3 sigma."""
+    L, n = 12, 1200
+    J = inputs.gaussian_couplings(L, seed=33)
+    with hsg.Lattice(L, 33) as lat:
+        lat.set_couplings(J)
+        lat.sweep(hsg.schedule(kind=hsg.HSG_METROPOLIS_OR, hits=2, proposal=1, T=0.7, energy_every=1), n)
+        g = lat.energy_log()
+    s = oracle.init_spins(L, 33)
+    _, r = oracle.sweeps(L, inputs.round_to_f32(J), s,
+                         oracle.Schedule(kind=oracle.MET_OR, hits=2, proposal=1, beta=1 / 0.7, energy_every=1),
+                         oracle.key(33), n)
+
+    def binned(x):
+        b = np.array([v.mean() for v in np.array_split(x[n // 5:], 20)])
+        return b.mean(), b.std(ddof=1) / np.sqrt(len(b))
+
+    mg, eg = binned(g)
+    mr, er = binned(r)
+    assert abs(mg - mr) < 3 * math.hypot(eg, er) + 1e-6, (mg, eg, mr, er)
+
+
 @pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("L,T", [(6, 1.0), (16, 0.3), (40, 0.3), (66, 1.0), (16, math.inf)])
 def test_heatbath_half_sweep_parity(hsg, variant, L, T):
@@ -321,14 +367,14 @@ def test_renorm_matches_oracle(hsg, scale):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("kind", ["HB", "MET"])
+@pytest.mark.parametrize("kind", ["HB", "MET", "METOR"])
 def test_sweep_is_the_composition_of_half_sweeps(hsg, variant, kind):
     """hsg_sweep = main update on colour 0 then 1, n_or OR sweeps, counter
     advance, renormalisation, energy log: bit-identical to issuing the same
     half-sweeps one by one."""
     L = 24
     J = inputs.gaussian_couplings(L, seed=19)
-    k = hsg.HSG_HEATBATH if kind == "HB" else hsg.HSG_METROPOLIS
+    k = {"HB": hsg.HSG_HEATBATH, "MET": hsg.HSG_METROPOLIS, "METOR": hsg.HSG_METROPOLIS_OR}[kind]
     sched = hsg.schedule(kind=k, hits=3, proposal=1, T=0.8, n_or=2, renorm_every=2, energy_every=1, kernel=variant)
     with hsg.Lattice(L, 19) as a:
         a.set_couplings(J)

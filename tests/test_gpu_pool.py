@@ -72,7 +72,7 @@ SPECS = [  # (L, seed, sample, replica, T)
 
 
 def base_schedule(hsg, kind):
-    k = hsg.HSG_METROPOLIS if kind == "MET" else hsg.HSG_HEATBATH
+    k = {"MET": hsg.HSG_METROPOLIS, "HB": hsg.HSG_HEATBATH, "METOR": hsg.HSG_METROPOLIS_OR}[kind]
     return dict(kind=k, hits=3, proposal=hsg.HSG_PROP_BALL, step=0.5, n_or=2, renorm_every=2)
 
 
@@ -87,7 +87,7 @@ def run_alone(hsg, spec, sched_kw, n, J=None):
         return lat.spins(), lat.energy()
 
 
-@pytest.mark.parametrize("kind", ["MET", "HB"])
+@pytest.mark.parametrize("kind", ["MET", "HB", "METOR"])
 @pytest.mark.parametrize("use_stream", [True, False])
 def test_pool_lattices_are_bit_identical_to_lattices_alone(hsg, kind, use_stream):
     kw = base_schedule(hsg, kind)

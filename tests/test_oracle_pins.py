@@ -486,3 +486,34 @@ def test_gaussian_couplings_are_standard_normal(orc):
         assert abs(np.corrcoef(Jm[:, a], Jm[:, b])[0, 1]) < 4 / np.sqrt(len(Jm))
     assert np.array_equal(J, orc.gaussian_couplings(L, seed=4, sample=7))
     assert not np.allclose(J, orc.gaussian_couplings(L, seed=4, sample=8))
+
+
+def test_fused_metropolis_over_relaxation_keeps_the_metropolis_energy(orc):
+    """The fused pass reflects the Metropolis result about the same field: the
+    site energy -s.h equals that of the Metropolis result alone, the
+    projection on h is kept, the perpendicular part flipped."""
+    rng = np.random.default_rng(12)
+    for t in range(200):
+        s = rng.standard_normal(3)
+        s /= np.linalg.norm(s)
+        h = rng.standard_normal(3) * 2
+        p = orc.Params(key=orc.key(12), sweep=t, beta=1.3, hits=3, proposal=orc.PROP_BALL, step=0.5)
+        met, m1 = orc.update_site(orc.MET, s, h, p, t, t % 2)
+        fused, m2 = orc.update_site(orc.MET_OR, s, h, p, t, t % 2)
+        assert m1 == m2
+        hh = h / np.linalg.norm(h)
+        assert abs(np.dot(fused, h) - np.dot(met, h)) < 1e-13
+        assert np.allclose(fused - np.dot(fused, hh) * hh, -(met - np.dot(met, hh) * hh), atol=1e-14)
+        assert abs(np.linalg.norm(fused) - 1) < 1e-12
+
+
+def test_fused_metropolis_over_relaxation_rings_give_langevin_energy(orc):
+    """The fused chain samples the Boltzmann distribution too: decoupled
+    rings at beta = 1.5 give E/N = -L(beta)."""
+    L, beta, n = 16, 1.5, 800
+    J = inputs.uniform_couplings(L, axes=(0,))
+    s = orc.init_spins(L, seed=3)
+    sch = orc.Schedule(kind=orc.MET_OR, proposal=orc.PROP_BALL, hits=2, step=0.5, beta=beta, energy_every=1)
+    _, elog = orc.sweeps(L, J, s, sch, orc.key(3), n)
+    mean, err = _binned_mean(elog[n // 5:])
+    assert abs(mean + langevin(beta)) < 3 * err + 1e-4, (mean, err)
