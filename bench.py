@@ -91,6 +91,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
+    ap.add_argument("--no-autotune", action="store_true", help="batched workload: default pool launch shape")
     return ap.parse_args()
 
 
@@ -519,7 +520,11 @@ def run_batched(args):
         for spec in specs:
             pool.admit(*spec)
         t0 = time.perf_counter()
-        cfg = hsg.hsg_pool_autotune(pool.pool, sched)
+        if args.no_autotune:
+            cfg = (256, 512, 8)  # the pool's default launch configuration
+            hsg.hsg_pool_config(pool.pool, *cfg)
+        else:
+            cfg = hsg.hsg_pool_autotune(pool.pool, sched)
         tune_s = time.perf_counter() - t0
         for _ in range(args.warmup):
             pool.sweep(sched, sps)

@@ -221,20 +221,24 @@ __device__ __forceinline__ float4 renorm_spin(float4 v) {
   return v;
 }
 
-// One site of a half-sweep: site (x = 2 xh + p, y, z) of colour `colour`
-// gathers its six other-colour neighbours and bonds (layout at the top of
-// this file), forms h (Eq. 2), applies update U and stores its new spin.
-// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.  Shared by every
-// half-sweep kernel that updates one site per thread, so that they give
-// bit-identical results.
+// What one site of a half-sweep reads: its six other-colour neighbours and
+// bonds, its own spin, its index q and its Philox site number.
+struct SiteInputs {
+  float4 sxp, sxm, syp, sym, szp, szm;
+  float jxp, jxm, jyp, jym, jzp, jzm;
+  float3 s;
+  uint32_t q, site;
+};
+
+// Gather the inputs of site (x = 2 xh + p, y, z) of colour `colour` (layout
+// at the top of this file).  Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.
 template <int U>
-__device__ __forceinline__ void half_sweep_site(float4* __restrict__ own, const float4* __restrict__ oth,
-                                                const float* __restrict__ jx_own, const float* __restrict__ jy_own,
-                                                const float* __restrict__ jz_own, const float* __restrict__ jx_oth,
-                                                const float* __restrict__ jy_oth, const float* __restrict__ jz_oth,
-                                                uint32_t xh, uint32_t y, uint32_t z, uint32_t L, uint32_t Lh,
-                                                uint32_t colour, uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
-                                                uint32_t k1, float beta, float step, int hits) {
+__device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __restrict__ own,
+                                            const float4* __restrict__ oth, const float* __restrict__ jx_own,
+                                            const float* __restrict__ jy_own, const float* __restrict__ jz_own,
+                                            const float* __restrict__ jx_oth, const float* __restrict__ jy_oth,
+                                            const float* __restrict__ jz_oth, uint32_t xh, uint32_t y, uint32_t z,
+                                            uint32_t L, uint32_t Lh, uint32_t colour) {
   const uint32_t p = (colour + y + z) & 1u;  // x = 2*xh + p
   const uint32_t plane = L * Lh;
   const uint32_t row = (z * L + y) * Lh;
@@ -245,21 +249,65 @@ __device__ __forceinline__ void half_sweep_site(float4* __restrict__ own, const 
   const uint32_t q_ym = y == 0 ? q + (L - 1) * Lh : q - Lh;
   const uint32_t q_zp = z + 1 == L ? q - (L - 1) * plane : q + plane;
   const uint32_t q_zm = z == 0 ? q + (L - 1) * plane : q - plane;
-  const float4 sxp = __ldg(oth + q_xp), sxm = __ldg(oth + q_xm);
-  const float4 syp = __ldg(oth + q_yp), sym = __ldg(oth + q_ym);
-  const float4 szp = __ldg(oth + q_zp), szm = __ldg(oth + q_zm);
-  const float jxp = __ldg(jx_own + q), jxm = __ldg(jx_oth + q_xm);
-  const float jyp = __ldg(jy_own + q), jym = __ldg(jy_oth + q_ym);
-  const float jzp = __ldg(jz_own + q), jzm = __ldg(jz_oth + q_zm);
-  float3 s = make_float3(0.0f, 0.0f, 0.0f);
+  in.sxp = __ldg(oth + q_xp);
+  in.sxm = __ldg(oth + q_xm);
+  in.syp = __ldg(oth + q_yp);
+  in.sym = __ldg(oth + q_ym);
+  in.szp = __ldg(oth + q_zp);
+  in.szm = __ldg(oth + q_zm);
+  in.jxp = __ldg(jx_own + q);
+  in.jxm = __ldg(jx_oth + q_xm);
+  in.jyp = __ldg(jy_own + q);
+  in.jym = __ldg(jy_oth + q_ym);
+  in.jzp = __ldg(jz_own + q);
+  in.jzm = __ldg(jz_oth + q_zm);
+  in.s = make_float3(0.0f, 0.0f, 0.0f);
   if constexpr (U != U_HB) {
     const float4 o = own[q];
-    s = make_float3(o.x, o.y, o.z);
+    in.s = make_float3(o.x, o.y, o.z);
   }
-  const float3 h = local_field(sxp, sxm, syp, sym, szp, szm, jxp, jxm, jyp, jym, jzp, jzm);
-  const uint32_t site = (2 * xh + p) + y * L + z * L * L;
-  const float3 t = update_site<U>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
-  own[q] = make_float4(t.x, t.y, t.z, 0.0f);
+  in.q = q;
+  in.site = (2 * xh + p) + y * L + z * L * L;
+}
+
+// Form h (Eq. 2), apply update U and store the site's new spin.
+template <int U>
+__device__ __forceinline__ void finish_site(const SiteInputs& in, float4* __restrict__ own, uint32_t colour,
+                                            uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0, uint32_t k1,
+                                            float beta, float step, int hits) {
+  const float3 h = local_field(in.sxp, in.sxm, in.syp, in.sym, in.szp, in.szm, in.jxp, in.jxm, in.jyp, in.jym,
+                               in.jzp, in.jzm);
+  const float3 t = update_site<U>(in.s, h, in.site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  own[in.q] = make_float4(t.x, t.y, t.z, 0.0f);
+}
+
+// One site of a half-sweep: gather, then finish.  Every half-sweep kernel
+// that updates sites one by one goes through gather_site / finish_site, so
+// they give bit-identical results.
+template <int U>
+__device__ __forceinline__ void half_sweep_site(float4* __restrict__ own, const float4* __restrict__ oth,
+                                                const float* __restrict__ jx_own, const float* __restrict__ jy_own,
+                                                const float* __restrict__ jz_own, const float* __restrict__ jx_oth,
+                                                const float* __restrict__ jy_oth, const float* __restrict__ jz_oth,
+                                                uint32_t xh, uint32_t y, uint32_t z, uint32_t L, uint32_t Lh,
+                                                uint32_t colour, uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
+                                                uint32_t k1, float beta, float step, int hits) {
+  SiteInputs in;
+  gather_site<U>(in, own, oth, jx_own, jy_own, jz_own, jx_oth, jy_oth, jz_oth, xh, y, z, L, Lh, colour);
+  finish_site<U>(in, own, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+}
+
+// Unsigned division by an invariant d (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, n / d = (t + ((n - t) >> s1)) >> s2
+// for every 32-bit n, where t = mulhi(m, n), s1 = min(l, 1), s2 = max(l - 1, 0).
+struct FastDiv {
+  uint32_t m, s1, s2;
+};
+
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) {
+  const uint32_t t = __umulhi(n, f.m);
+  return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 
 __device__ __forceinline__ int wrap_inc(int v, int n) { return v + 1 == n ? 0 : v + 1; }

@@ -28,7 +28,7 @@
 
 namespace {
 
-// One slot as the kernels see it (64 bytes).
+// One slot as the kernels see it (96 bytes).
 struct PoolDesc {
   uint32_t L, Lh, nh, plane;          // side, side/2, sites per colour, per colour-plane
   uint32_t k0, k1;                    // Philox key of (seed, sample, replica)
@@ -38,8 +38,25 @@ struct PoolDesc {
   uint32_t tile_begin, tile_count;    // the slot's tiles in the work list
   unsigned long long spin_off;        // float4 offset of colour 0 (colour 1 at + nh)
   unsigned long long j_off;           // float offset of J[0][0] (J[d][c] at + (2d + c) nh)
+  hsg::FastDiv by_plane, by_lh;       // division of a site index by plane and by Lh
+  uint32_t pad[2];
 };
-static_assert(sizeof(PoolDesc) == 64, "PoolDesc layout");
+static_assert(sizeof(PoolDesc) == 96, "PoolDesc layout");
+
+hsg::FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;  // ceil(log2 d)
+  const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return hsg::FastDiv{(uint32_t)m, l < 1 ? l : 1u, l > 1 ? l - 1 : 0u};
+}
+
+// Site index q -> (xh, y, z) of a slot.
+__device__ __forceinline__ void decode_site(const PoolDesc* d, uint32_t q, uint32_t& xh, uint32_t& y, uint32_t& z) {
+  z = hsg::fast_div(q, d->by_plane);
+  const uint32_t r = q - z * d->plane;
+  y = hsg::fast_div(r, d->by_lh);
+  xh = r - y * d->Lh;
+}
 
 constexpr size_t kAlign = 256;
 
@@ -55,21 +72,43 @@ __global__ void __launch_bounds__(256) k_pool_half_sweep(const PoolDesc* __restr
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const uint2 tl = tiles[t];
     const PoolDesc* d = desc + tl.x;
-    const uint32_t L = d->L, Lh = d->Lh, nh = d->nh, plane = d->plane;
+    const uint32_t L = d->L, Lh = d->Lh, nh = d->nh;
     float4* base = S + d->spin_off;
     float4* own = base + (colour ? nh : 0);
     const float4* oth = base + (colour ? 0 : nh);
     const float* j = J + d->j_off;
     const uint32_t o = 1u - colour;
-    for (uint32_t k = threadIdx.x; k < tile_sites; k += blockDim.x) {
-      const uint32_t q = tl.y + k;
-      if (q >= nh) break;
-      const uint32_t z = q / plane, r = q - z * plane;
-      const uint32_t y = r / Lh, xh = r - y * Lh;
-      hsg::half_sweep_site<U>(own, oth, j + (0 + colour) * nh, j + (2 + colour) * (size_t)nh,
-                              j + (4 + colour) * (size_t)nh, j + (0 + o) * nh, j + (2 + o) * (size_t)nh,
-                              j + (4 + o) * (size_t)nh, xh, y, z, L, Lh, colour, d->sweep_lo, d->sweep_hi, d->k0,
-                              d->k1, d->beta, step, hits);
+    const float *jxo = j + (0 + colour) * (size_t)nh, *jyo = j + (2 + colour) * (size_t)nh,
+                *jzo = j + (4 + colour) * (size_t)nh, *jxt = j + (0 + o) * (size_t)nh,
+                *jyt = j + (2 + o) * (size_t)nh, *jzt = j + (4 + o) * (size_t)nh;
+    if constexpr (U == hsg::U_OR) {
+      // Memory-bound: keep two sites' loads in flight per thread.
+      for (uint32_t k = threadIdx.x; k < tile_sites; k += 2 * blockDim.x) {
+        const uint32_t qa = tl.y + k, kb = k + blockDim.x, qb = tl.y + kb;
+        const bool va = qa < nh, vb = kb < tile_sites && qb < nh;
+        hsg::SiteInputs a, b;
+        uint32_t xh, y, z;
+        if (va) {
+          decode_site(d, qa, xh, y, z);
+          hsg::gather_site<U>(a, own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour);
+        }
+        if (vb) {
+          decode_site(d, qb, xh, y, z);
+          hsg::gather_site<U>(b, own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour);
+        }
+        if (va) hsg::finish_site<U>(a, own, colour, 0u, 0u, 0u, 0u, 0.0f, step, hits);
+        if (vb) hsg::finish_site<U>(b, own, colour, 0u, 0u, 0u, 0u, 0.0f, step, hits);
+        if (!vb) break;
+      }
+    } else {
+      for (uint32_t k = threadIdx.x; k < tile_sites; k += blockDim.x) {
+        const uint32_t q = tl.y + k;
+        if (q >= nh) break;
+        uint32_t xh, y, z;
+        decode_site(d, q, xh, y, z);
+        hsg::half_sweep_site<U>(own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour, d->sweep_lo,
+                                d->sweep_hi, d->k0, d->k1, d->beta, step, hits);
+      }
     }
   }
 }
@@ -146,8 +185,8 @@ __global__ void __launch_bounds__(256) k_pool_energy_partial(const PoolDesc* __r
     for (uint32_t k = threadIdx.x; k < tile_sites; k += blockDim.x) {
       const uint32_t q = tl.y + k;
       if (q >= nh) break;
-      const uint32_t z = q / plane, r = q - z * plane;
-      const uint32_t y = r / Lh, xh = r - y * Lh;
+      uint32_t xh, y, z;
+      decode_site(d, q, xh, y, z);
       const uint32_t p = (y + z) & 1u;
       const uint32_t row = (z * L + y) * Lh;
       const uint32_t q_xp = p ? (xh + 1 == Lh ? row : q + 1) : q;
@@ -340,6 +379,8 @@ hsg_status sync_tables(hsg_pool* p) {
     d.active = 1;
     d.spin_off = s.off / sizeof(float4);
     d.j_off = (s.off + sizeof(float4) * n) / sizeof(float);
+    d.by_plane = make_fastdiv(d.plane);
+    d.by_lh = make_fastdiv(d.Lh);
     d.tile_begin = nt;
     for (uint32_t q0 = 0; q0 < d.nh; q0 += (uint32_t)p->tile_sites) p->h_tiles[nt++] = make_uint2((uint32_t)i, q0);
     d.tile_count = nt - d.tile_begin;
