@@ -44,6 +44,9 @@ import numpy as np  # noqa: E402
 #   heat-bath: own spin write 16, neighbours 16, bonds 24 (old spin not read)
 #   energy: 28 per site (all spins 16, all bonds 12); renormalisation: 32 per site
 BYTES_OR, BYTES_HB, BYTES_ENERGY, BYTES_RENORM = 72, 56, 28, 32
+# Temporally blocked over-relaxation sweep (both colours in one pass), per
+# site update: all spins read 16 + written 16, all bonds 12.
+BYTES_OR_WAVE = 44
 
 WORKLOADS = {
     "l256_hb_or": dict(
@@ -87,7 +90,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serving"], default="l256_hb_or")
-    ap.add_argument("--kernel", choices=["auto", "global", "slab"], default="auto")
+    ap.add_argument("--kernel", choices=["auto", "global", "slab", "wave"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
@@ -179,7 +182,7 @@ def measured_peaks():
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("hsg_sweep.cu", "hsg_device.cuh"):
+    for f in ("hsg_sweep.cu", "hsg_wave.cu", "hsg_device.cuh"):
         with open(os.path.join(ROOT, "paper_1006_2566_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -188,7 +191,8 @@ def kernel_source_hash() -> str:
 def profiled_traffic(kernel_variant: str, L: int):
     """DRAM bytes per over-relaxation launch from the committed ncu summary,
     if it was taken on the current kernel source; else None."""
-    path = os.path.join(ROOT, "profiles", f"or_half_sweep_{kernel_variant}_L{L}.md")
+    name = f"or_full_sweep_wave_L{L}.md" if kernel_variant == "wave" else f"or_half_sweep_{kernel_variant}_L{L}.md"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
@@ -205,10 +209,10 @@ def step_units(wl) -> int:
     return (wl["L"] ** 3) * passes * wl["sweeps_per_step"]
 
 
-def step_bytes(wl) -> int:
+def step_bytes(wl, wave: bool = False) -> int:
     n = wl["L"] ** 3
     main = {"HB": BYTES_HB, "MET": BYTES_OR, "METOR": BYTES_OR}.get(wl["kind"], 0)
-    per_sweep = n * (main + wl["n_or"] * BYTES_OR)
+    per_sweep = n * (main + wl["n_or"] * (BYTES_OR_WAVE if wave else BYTES_OR))
     s = wl["sweeps_per_step"]
     extra = 0
     if wl["energy_every"]:
@@ -245,7 +249,8 @@ def run_ours(args, wl):
     kind = {"HB": hsg.HSG_HEATBATH, "MET": hsg.HSG_METROPOLIS, "METOR": hsg.HSG_METROPOLIS_OR,
             "NONE": hsg.HSG_NONE}[wl["kind"]]
     proposal = {"SPHERE": hsg.HSG_PROP_SPHERE, "BALL": hsg.HSG_PROP_BALL}[wl["proposal"]]
-    kernel = {"auto": hsg.HSG_KERNEL_AUTO, "global": hsg.HSG_KERNEL_GLOBAL, "slab": hsg.HSG_KERNEL_SLAB}[args.kernel]
+    kernel = {"auto": hsg.HSG_KERNEL_AUTO, "global": hsg.HSG_KERNEL_GLOBAL, "slab": hsg.HSG_KERNEL_SLAB,
+              "wave": hsg.HSG_KERNEL_WAVE}[args.kernel]
     sched = hsg.schedule(kind=kind, hits=wl["hits"], proposal=proposal, step=wl["step"], n_or=wl["n_or"], T=wl["T"],
                          renorm_every=wl["renorm_every"], energy_every=wl["energy_every"], kernel=kernel)
     sps = wl["sweeps_per_step"]
@@ -254,6 +259,7 @@ def run_ours(args, wl):
     J = inputs.gaussian_couplings(L, seed=wl["seed"], sample=sample, dtype=np.float32)
     lat = hsg.Lattice(L, wl["seed"], sample, 0, stream)
     lat.set_couplings(J)
+    kernel_used = hsg.hsg_kernel_for(lat.ctx, sched)  # what HSG_KERNEL_AUTO resolves to
     # inputs resident in HBM from here on
     for _ in range(args.warmup):
         lat.sweep(sched, sps)
@@ -340,32 +346,45 @@ def run_ours(args, wl):
     hb_ms, hb_n = per_class[hsg.HSG_PROF_HEATBATH]
     met_ms, met_n = per_class[hsg.HSG_PROF_METROPOLIS]
     nh = N // 2
-    variant = {"auto": "global", "global": "global", "slab": "slab"}[args.kernel]
+    variant = {hsg.HSG_KERNEL_GLOBAL: "global", hsg.HSG_KERNEL_SLAB: "slab",
+               hsg.HSG_KERNEL_WAVE: "wave"}[kernel_used]
+    wave = variant == "wave"
+    # Units one over-relaxation launch processes: N/2 sites per half-sweep,
+    # N per wave sweep.
+    units = N if wave else nh
+    b_or = BYTES_OR_WAVE if wave else BYTES_OR
     roof = None
     if or_n:
-        alg = nh * BYTES_OR
+        alg = units * b_or
         avg_s = or_ms / or_n / 1e3
         ach = alg / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": "over-relaxation half-sweep", "achieved": round(ach, 1),
+        kname = "over-relaxation full sweep, temporally blocked" if wave else "over-relaxation half-sweep"
+        roof = {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": profiled_traffic(variant, L), "algorithmic_bytes_per_launch": alg,
                 "avg_launch_ms": round(or_ms / or_n, 5), "launches": or_n,
                 "frac_of_nominal_8TBps": round(ach / 8000.0, 4),
+                # The rate the single-pass byte model (72 B per site update,
+                # one pass per colour) would need for the same sweep time.
+                "single_pass_equivalent": ({"bytes_per_update": BYTES_OR,
+                                            "GBps": round(units * BYTES_OR / avg_s / 1e9, 1),
+                                            "frac": round(units * BYTES_OR / avg_s / 1e9 / peak, 4)}
+                                           if wave else None),
                 "measured_over": f"{args.steps} steps with per-launch CUDA events ({profiled_ms / args.steps:.3f} "
                                  f"ms/step, directly launched)"}
     kernels = {}
-    for name, (ms, n), bpu in (("heatbath", (hb_ms, hb_n), BYTES_HB), ("overrelax", (or_ms, or_n), BYTES_OR),
-                               ("metropolis", (met_ms, met_n), BYTES_OR)):
+    for name, (ms, n), bpu, u in (("heatbath", (hb_ms, hb_n), BYTES_HB, nh), ("overrelax", (or_ms, or_n), b_or, units),
+                                  ("metropolis", (met_ms, met_n), BYTES_OR, nh)):
         if n:
             kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
-                             "GBps": round(nh * bpu / (ms / n / 1e3) / 1e9, 1)}
+                             "GBps": round(u * bpu / (ms / n / 1e3) / 1e9, 1)}
     for name, k in (("energy", hsg.HSG_PROF_ENERGY), ("renorm", hsg.HSG_PROF_RENORM)):
         ms, n = per_class[k]
         if n:
             bpu = BYTES_ENERGY if name == "energy" else BYTES_RENORM
             kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
                              "GBps": round(N * bpu / (ms / n / 1e3) / 1e9, 1)}
-    step_gbps = step_bytes(wl) / (elapsed_ms / args.steps / 1e3) / 1e9
+    step_gbps = step_bytes(wl, wave) / (elapsed_ms / args.steps / 1e3) / 1e9
     out = {
         "metric": "spin updates/ns", "value": round(value, 4), "unit": "spin updates/ns", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
@@ -376,7 +395,7 @@ def run_ours(args, wl):
                    "l2": "inputs larger than L2 (state 470 MB vs 126 MB L2), no flush" if L >= 256 else
                          "state fits in L2"},
         "roofline": roof,
-        "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes(wl),
+        "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes(wl, wave),
                           "achieved_GBps": round(step_gbps, 1), "frac": round(step_gbps / peak, 4)},
         "kernels": kernels,
         "gpu_launches": int(launches),

@@ -73,9 +73,21 @@ enum { HSG_HOST = 0, HSG_DEVICE = 1 };
 
 /* Half-sweep kernel variant. */
 enum {
-  HSG_KERNEL_AUTO = 0,   /* library's choice for the lattice size */
+  HSG_KERNEL_AUTO = 0,   /* library's choice: HSG_KERNEL_WAVE when the lattice's
+                          * spins and bonds (28 N bytes) exceed the device's L2,
+                          * so that the sweep streams from HBM; else GLOBAL */
   HSG_KERNEL_GLOBAL = 1, /* one thread per site, neighbours through L1/L2 */
-  HSG_KERNEL_SLAB = 2    /* z-marching tiles: other colour staged in shared memory */
+  HSG_KERNEL_SLAB = 2,   /* z-marching tiles: other colour staged in shared memory */
+  /* Temporally blocked over-relaxation: each over-relaxation sweep
+   * runs colour 0 and colour 1 in ONE pass over the lattice (z-marching
+   * tiles; the new colour-0 planes stay in shared memory for the colour-1
+   * update), so each spin and bond leaves HBM about once per sweep instead of
+   * once per half-sweep (44 instead of 72 bytes per site update).  Results
+   * are bit-identical to HSG_KERNEL_GLOBAL.  The pass writes a second spin
+   * buffer of 16 N bytes, allocated by the first hsg_sweep that needs it and
+   * kept until hsg_destroy; the two buffers alternate.  The main update of a
+   * sweep and hsg_half_sweep use the global kernel. */
+  HSG_KERNEL_WAVE = 3
 };
 
 /* Kernel classes reported by the profiler. */
@@ -215,6 +227,14 @@ hsg_status hsg_half_sweep(hsg_ctx* ctx, const hsg_schedule* schedule, int update
 
 /* Renormalise every spin, s <- s/|s|, computed in FP64, stored FP32. */
 hsg_status hsg_renorm(hsg_ctx* ctx);
+
+/*
+ * The kernel variant hsg_sweep runs for the over-relaxation sweeps of
+ * `schedule` on this lattice (HSG_KERNEL_GLOBAL, _SLAB or _WAVE: what
+ * HSG_KERNEL_AUTO resolves to).  Library-specific; the paper has no
+ * counterpart.  Errors: HSG_EINVAL (NULL argument, bad schedule).
+ */
+hsg_status hsg_kernel_for(hsg_ctx* ctx, const hsg_schedule* schedule, int* kernel);
 
 /*
  * Profiler: with on != 0 every kernel the context launches is bracketed

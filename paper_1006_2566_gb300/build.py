@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhsg.so")
-SOURCES = ["hsg_sweep.cu", "hsg_aux.cu", "hsg_api.cu", "hsg_noalloc.cu", "hsg_pool.cu"]
+SOURCES = ["hsg_sweep.cu", "hsg_aux.cu", "hsg_api.cu", "hsg_noalloc.cu", "hsg_pool.cu", "hsg_wave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2", "-I", INCLUDE, "-I", CSRC] + ARCH
 

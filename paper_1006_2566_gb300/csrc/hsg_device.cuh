@@ -61,11 +61,12 @@ __device__ __forceinline__ float3 sphere_point(float u0, float u1) {
 __device__ __forceinline__ float dot3(float3 a, float3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 
 // Over-relaxation: reflection of s about h, s' = 2 (s.h)/(h.h) h - s;
-// unchanged when h = 0.
+// unchanged when h = 0.  The quotient takes the fast divide (2 ulp; h.h is
+// at most (sum |J|)^2, far below the 2^126 where it would flush to 0).
 __device__ __forceinline__ float3 update_or(float3 s, float3 h) {
   const float hh = dot3(h, h);
   if (hh == 0.0f) return s;
-  const float f = 2.0f * dot3(s, h) / hh;
+  const float f = __fdividef(2.0f * dot3(s, h), hh);
   return make_float3(fmaf(f, h.x, -s.x), fmaf(f, h.y, -s.y), fmaf(f, h.z, -s.z));
 }
 
@@ -270,15 +271,23 @@ __device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __rest
   in.site = (2 * xh + p) + y * L + z * L * L;
 }
 
-// Form h (Eq. 2), apply update U and store the site's new spin.
+// Form h (Eq. 2) and apply update U: the site's new spin.
+template <int U>
+__device__ __forceinline__ float4 site_result(const SiteInputs& in, uint32_t colour, uint32_t sweep_lo,
+                                              uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta, float step,
+                                              int hits) {
+  const float3 h = local_field(in.sxp, in.sxm, in.syp, in.sym, in.szp, in.szm, in.jxp, in.jxm, in.jyp, in.jym,
+                               in.jzp, in.jzm);
+  const float3 t = update_site<U>(in.s, h, in.site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  return make_float4(t.x, t.y, t.z, 0.0f);
+}
+
+// Form h, apply update U and store the site's new spin.
 template <int U>
 __device__ __forceinline__ void finish_site(const SiteInputs& in, float4* __restrict__ own, uint32_t colour,
                                             uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0, uint32_t k1,
                                             float beta, float step, int hits) {
-  const float3 h = local_field(in.sxp, in.sxm, in.syp, in.sym, in.szp, in.szm, in.jxp, in.jxm, in.jyp, in.jym,
-                               in.jzp, in.jzm);
-  const float3 t = update_site<U>(in.s, h, in.site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
-  own[in.q] = make_float4(t.x, t.y, t.z, 0.0f);
+  own[in.q] = site_result<U>(in, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
 }
 
 // One site of a half-sweep: gather, then finish.  Every half-sweep kernel

@@ -29,11 +29,24 @@ struct SweepArgs {
 };
 
 // Kernel variants (values match HSG_KERNEL_*).
-enum Variant : int { V_AUTO = 0, V_GLOBAL = 1, V_SLAB = 2 };
+enum Variant : int { V_AUTO = 0, V_GLOBAL = 1, V_SLAB = 2, V_WAVE = 3 };
 
 // Half-sweep of update kind `upd` (UpdKind) with kernel `variant`
 // (V_GLOBAL or V_SLAB).  One kernel launch.
 cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, cudaStream_t s);
+
+// Arguments of one temporally blocked over-relaxation sweep (hsg_wave.cu):
+// colour 0 then colour 1, read from `src` and written to `dst`.
+struct WaveArgs {
+  const float4* src;  // S[2][N/2] before the sweep
+  float4* dst;        // S[2][N/2] after the sweep; must not overlap src
+  const float* J;     // J[3][2][N/2]
+  int L, Lh;
+};
+
+// Over-relaxation sweep (both colours) in one launch, bit-identical to the
+// colour-0 and colour-1 half-sweeps of launch_half_sweep(U_OR, ...).
+cudaError_t launch_or_sweep_wave(const WaveArgs& a, int sm_count, cudaStream_t s);
 
 // Spin initialisation: S[2][N/2] from Philox kind INIT.  One launch.
 cudaError_t launch_init_spins(float4* S, int L, uint32_t k0, uint32_t k1, cudaStream_t s);

@@ -23,7 +23,7 @@ HSG_NONE, HSG_METROPOLIS, HSG_HEATBATH, HSG_OVERRELAX, HSG_METROPOLIS_OR = range
 HSG_PROP_SPHERE, HSG_PROP_BALL = 0, 1
 HSG_F32, HSG_F64 = 0, 1
 HSG_HOST, HSG_DEVICE = 0, 1
-HSG_KERNEL_AUTO, HSG_KERNEL_GLOBAL, HSG_KERNEL_SLAB = 0, 1, 2
+HSG_KERNEL_AUTO, HSG_KERNEL_GLOBAL, HSG_KERNEL_SLAB, HSG_KERNEL_WAVE = 0, 1, 2, 3
 (HSG_PROF_INIT, HSG_PROF_LAYOUT, HSG_PROF_OVERRELAX, HSG_PROF_METROPOLIS, HSG_PROF_HEATBATH,
  HSG_PROF_ENERGY, HSG_PROF_RENORM, HSG_PROF_COUNT) = range(8)
 
@@ -78,6 +78,7 @@ _SIGS = {
     "hsg_set_sweep": ([_vp, _u64], _i),
     "hsg_half_sweep": ([_vp, _sch_p, _i, _i], _i),
     "hsg_renorm": ([_vp], _i),
+    "hsg_kernel_for": ([_vp, _sch_p, ctypes.POINTER(_i)], _i),
     "hsg_profile": ([_vp, _i], _i),
     "hsg_profile_read": ([_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_u64)], _i),
     "hsg_profile_reset": ([_vp], _i),
@@ -230,6 +231,13 @@ def hsg_half_sweep(ctx, sched: hsg_schedule, update: int, colour: int) -> None:
 
 def hsg_renorm(ctx) -> None:
     _check(_lib.hsg_renorm(ctx), ctx)
+
+
+def hsg_kernel_for(ctx, sched: hsg_schedule) -> int:
+    """The HSG_KERNEL_* variant hsg_sweep runs for the OR sweeps of `sched`."""
+    k = _i(0)
+    _check(_lib.hsg_kernel_for(ctx, ctypes.byref(sched), ctypes.byref(k)), ctx)
+    return k.value
 
 
 def hsg_profile(ctx, on: bool) -> None:
