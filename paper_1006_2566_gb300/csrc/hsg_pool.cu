@@ -62,8 +62,13 @@ constexpr size_t kAlign = 256;
 
 inline unsigned cdiv_u(unsigned long long a, unsigned long long b) { return (unsigned)((a + b - 1) / b); }
 
+// At most 64 registers (four CTAs of 256 threads per SM): the over-relaxation
+// pass is memory-bound and needs the resident warps for loads in flight
+// (measured on GB300, 39 M sites: 350 us per half-sweep at 120 registers and
+// two sites per thread, 243 us at 56 registers and one), and the Metropolis
+// pass runs fastest at the 64 registers its code wants.
 template <int U>
-__global__ void __launch_bounds__(256) k_pool_half_sweep(const PoolDesc* __restrict__ desc,
+__global__ void __launch_bounds__(256, 4) k_pool_half_sweep(const PoolDesc* __restrict__ desc,
                                                          const uint2* __restrict__ tiles,
                                                          const uint32_t* __restrict__ n_tiles, float4* __restrict__ S,
                                                          const float* __restrict__ J, uint32_t colour, float step,
@@ -81,34 +86,13 @@ __global__ void __launch_bounds__(256) k_pool_half_sweep(const PoolDesc* __restr
     const float *jxo = j + (0 + colour) * (size_t)nh, *jyo = j + (2 + colour) * (size_t)nh,
                 *jzo = j + (4 + colour) * (size_t)nh, *jxt = j + (0 + o) * (size_t)nh,
                 *jyt = j + (2 + o) * (size_t)nh, *jzt = j + (4 + o) * (size_t)nh;
-    if constexpr (U == hsg::U_OR) {
-      // Memory-bound: keep two sites' loads in flight per thread.
-      for (uint32_t k = threadIdx.x; k < tile_sites; k += 2 * blockDim.x) {
-        const uint32_t qa = tl.y + k, kb = k + blockDim.x, qb = tl.y + kb;
-        const bool va = qa < nh, vb = kb < tile_sites && qb < nh;
-        hsg::SiteInputs a, b;
-        uint32_t xh, y, z;
-        if (va) {
-          decode_site(d, qa, xh, y, z);
-          hsg::gather_site<U>(a, own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour);
-        }
-        if (vb) {
-          decode_site(d, qb, xh, y, z);
-          hsg::gather_site<U>(b, own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour);
-        }
-        if (va) hsg::finish_site<U>(a, own, colour, 0u, 0u, 0u, 0u, 0.0f, step, hits);
-        if (vb) hsg::finish_site<U>(b, own, colour, 0u, 0u, 0u, 0u, 0.0f, step, hits);
-        if (!vb) break;
-      }
-    } else {
-      for (uint32_t k = threadIdx.x; k < tile_sites; k += blockDim.x) {
-        const uint32_t q = tl.y + k;
-        if (q >= nh) break;
-        uint32_t xh, y, z;
-        decode_site(d, q, xh, y, z);
-        hsg::half_sweep_site<U>(own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour, d->sweep_lo,
-                                d->sweep_hi, d->k0, d->k1, d->beta, step, hits);
-      }
+    for (uint32_t k = threadIdx.x; k < tile_sites; k += blockDim.x) {
+      const uint32_t q = tl.y + k;
+      if (q >= nh) break;
+      uint32_t xh, y, z;
+      decode_site(d, q, xh, y, z);
+      hsg::half_sweep_site<U>(own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour, d->sweep_lo,
+                              d->sweep_hi, d->k0, d->k1, d->beta, step, hits);
     }
   }
 }
