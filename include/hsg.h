@@ -204,6 +204,18 @@ hsg_status hsg_get_energy_log(hsg_ctx* ctx, double* out, int max_n, int* n);
 hsg_status hsg_clear_energy_log(hsg_ctx* ctx);
 
 /*
+ * Spins and bonds of n listed sites (site-major indices i = x + y*L +
+ * z*L*L < N, host array `sites`): spins[3k + a] = component a of site
+ * sites[k], and, if `bonds` is not NULL, bonds[3k + d] = J of its bond to
+ * +e_d (d = 0, 1, 2).  Host output arrays of 3n floats; synchronises the
+ * stream.  For checking samples of lattices too large to copy whole
+ * (library-specific; the paper has no counterpart).
+ * Errors: HSG_EINVAL (NULL arrays with n > 0, n < 0, an index >= N, bonds
+ * requested before couplings are set).
+ */
+hsg_status hsg_get_sites(hsg_ctx* ctx, const uint32_t* sites, int n, float* spins, float* bonds);
+
+/*
  * Spins as site-major FP32 s[3*N] (see top), in memory space `where`.
  * hsg_get_spins with HSG_HOST synchronises; with HSG_DEVICE it is queued
  * on the stream.  hsg_set_spins stores the values as given (no

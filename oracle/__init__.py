@@ -80,7 +80,11 @@ def _load():
         lib.oracle_colour.argtypes = [ctypes.c_int, ctypes.c_int64]
         lib.oracle_init_spins.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _dp]
         lib.oracle_gaussian_couplings.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, _dp]
+        lib.oracle_init_spin_sites.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _u32p,
+                                               ctypes.c_int, _dp]
+        lib.oracle_gaussian_coupling_sites.argtypes = [ctypes.c_uint64, ctypes.c_uint32, _u32p, ctypes.c_int, _dp]
         lib.oracle_local_field.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int64, _dp]
+        lib.oracle_local_field_nb.argtypes = [_dp, _dp, _dp]
         lib.oracle_energy.argtypes = [ctypes.c_int, _dp, _dp]
         lib.oracle_energy.restype = ctypes.c_double
         lib.oracle_update_site.argtypes = [ctypes.c_int, _dp, _dp, ctypes.POINTER(_Params), ctypes.c_uint32,
@@ -183,9 +187,37 @@ def gaussian_couplings(L: int, seed: int, sample: int = 0) -> np.ndarray:
     return J
 
 
+def init_spin_sites(sites, seed: int, sample: int = 0, replica: int = 0) -> np.ndarray:
+    """Initial spins (n, 3) of listed site-major indices (any lattice size)."""
+    idx = np.ascontiguousarray(np.asarray(sites, dtype=np.uint32).reshape(-1))
+    out = np.zeros(3 * idx.size, dtype=np.float64)
+    _load().oracle_init_spin_sites(int(seed), int(sample), int(replica),
+                                   idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), idx.size, _d(out))
+    return out.reshape(-1, 3)
+
+
+def gaussian_coupling_sites(sites, seed: int, sample: int = 0) -> np.ndarray:
+    """+x/+y/+z couplings (n, 3) of listed site-major indices (any lattice size)."""
+    idx = np.ascontiguousarray(np.asarray(sites, dtype=np.uint32).reshape(-1))
+    out = np.zeros(3 * idx.size, dtype=np.float64)
+    _load().oracle_gaussian_coupling_sites(int(seed), int(sample), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
+                                           idx.size, _d(out))
+    return out.reshape(-1, 3)
+
+
 def local_field(L: int, J: np.ndarray, s: np.ndarray, i: int) -> np.ndarray:
     h = np.zeros(3, dtype=np.float64)
     _load().oracle_local_field(int(L), _d(J), _d(s), int(i), _d(h))
+    return h
+
+
+def local_field_nb(nb: np.ndarray, Jb: np.ndarray) -> np.ndarray:
+    """Eq. 2 from explicit neighbours: nb (6, 3) spins at +x, -x, +y, -y, +z,
+    -z and Jb (6,) the bonds to them (oracle_local_field's order)."""
+    nb = np.ascontiguousarray(nb, dtype=np.float64).reshape(18)
+    Jb = np.ascontiguousarray(Jb, dtype=np.float64).reshape(6)
+    h = np.zeros(3, dtype=np.float64)
+    _load().oracle_local_field_nb(_d(nb), _d(Jb), _d(h))
     return h
 
 

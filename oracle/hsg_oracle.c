@@ -167,15 +167,28 @@ int oracle_colour(int L, int64_t i) {
 
 /* Spin initialisation: site i takes the sphere point of the draw
  * (site = i, sweep 0, kind INIT, colour 0, hit 0). */
+/* Initial spin of site i under key `key`: the sphere map of the Philox draw
+ * at counter (i, 0, INIT<<24, 0). */
+static void init_spin_at(const uint32_t key[2], uint32_t i, double out[3]) {
+  uint32_t ctr[4], r[4];
+  oracle_counter(i, 0, ORACLE_KIND_INIT, 0, 0, ctr);
+  oracle_philox4x32_10(ctr, key, r);
+  sphere_point(oracle_u01(r[0]), oracle_u01(r[1]), out);
+}
+
 void oracle_init_spins(int L, uint64_t seed, uint32_t sample, uint32_t replica, double* s) {
-  uint32_t key[2], ctr[4], r[4];
+  uint32_t key[2];
   int64_t n = (int64_t)L * L * L;
   oracle_key(seed, sample, replica, key);
-  for (int64_t i = 0; i < n; ++i) {
-    oracle_counter((uint32_t)i, 0, ORACLE_KIND_INIT, 0, 0, ctr);
-    oracle_philox4x32_10(ctr, key, r);
-    sphere_point(oracle_u01(r[0]), oracle_u01(r[1]), &s[3 * i]);
-  }
+  for (int64_t i = 0; i < n; ++i) init_spin_at(key, (uint32_t)i, &s[3 * i]);
+}
+
+/* The same for n listed sites (any lattice size): out[3k..3k+2] = spin of sites[k]. */
+void oracle_init_spin_sites(uint64_t seed, uint32_t sample, uint32_t replica, const uint32_t* sites, int n,
+                            double* out) {
+  uint32_t key[2];
+  oracle_key(seed, sample, replica, key);
+  for (int k = 0; k < n; ++k) init_spin_at(key, sites[k], &out[3 * k]);
 }
 
 /* Gaussian couplings J ~ N(0,1) (Sec. 2: Gaussian, mean 0, variance 1),
@@ -186,20 +199,30 @@ void oracle_init_spins(int L, uint64_t seed, uint32_t sample, uint32_t replica, 
  *   J[3i]   = sqrt(-2 ln u0) cos(2 pi u1),
  *   J[3i+1] = sqrt(-2 ln u0) sin(2 pi u1),
  *   J[3i+2] = sqrt(-2 ln u2) cos(2 pi u3). */
+static void couplings_at(const uint32_t key[2], uint32_t i, double out[3]) {
+  uint32_t ctr[4], r[4];
+  oracle_counter(i, 0, ORACLE_KIND_JGEN, 0, 0, ctr);
+  oracle_philox4x32_10(ctr, key, r);
+  double u0 = oracle_u01(r[0]), u1 = oracle_u01(r[1]);
+  double u2 = oracle_u01(r[2]), u3 = oracle_u01(r[3]);
+  double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
+  out[0] = a * cos(2.0 * ORACLE_PI * u1);
+  out[1] = a * sin(2.0 * ORACLE_PI * u1);
+  out[2] = b * cos(2.0 * ORACLE_PI * u3);
+}
+
 void oracle_gaussian_couplings(int L, uint64_t seed, uint32_t sample, double* J) {
-  uint32_t key[2], ctr[4], r[4];
+  uint32_t key[2];
   int64_t n = (int64_t)L * L * L;
   oracle_key(seed, sample, 0, key);
-  for (int64_t i = 0; i < n; ++i) {
-    oracle_counter((uint32_t)i, 0, ORACLE_KIND_JGEN, 0, 0, ctr);
-    oracle_philox4x32_10(ctr, key, r);
-    double u0 = oracle_u01(r[0]), u1 = oracle_u01(r[1]);
-    double u2 = oracle_u01(r[2]), u3 = oracle_u01(r[3]);
-    double a = sqrt(-2.0 * log(u0)), b = sqrt(-2.0 * log(u2));
-    J[3 * i] = a * cos(2.0 * ORACLE_PI * u1);
-    J[3 * i + 1] = a * sin(2.0 * ORACLE_PI * u1);
-    J[3 * i + 2] = b * cos(2.0 * ORACLE_PI * u3);
-  }
+  for (int64_t i = 0; i < n; ++i) couplings_at(key, (uint32_t)i, &J[3 * i]);
+}
+
+/* The same for n listed sites: out[3k + d] = J of the bond from sites[k] to +e_d. */
+void oracle_gaussian_coupling_sites(uint64_t seed, uint32_t sample, const uint32_t* sites, int n, double* out) {
+  uint32_t key[2];
+  oracle_key(seed, sample, 0, key);
+  for (int k = 0; k < n; ++k) couplings_at(key, sites[k], &out[3 * k]);
 }
 
 /* Local field of site i (Eq. 2 with reading R2):
@@ -213,6 +236,17 @@ void oracle_local_field(int L, const double* J, const double* s, int64_t i, doub
     double j_dn = J[3 * dn + d];
     for (int a = 0; a < 3; ++a) h[a] += j_up * s[3 * up + a] + j_dn * s[3 * dn + a];
   }
+}
+
+/* The same sum for one site from its six neighbours given explicitly (for
+   samples of lattices too large to hold): for d = x, y, z in turn, nb[2d] is
+   the spin at i + e_d with bond Jb[2d] = J[3i + d], nb[2d + 1] the spin at
+   i - e_d with bond Jb[2d + 1] = J[3(i - e_d) + d]; same order of terms as
+   oracle_local_field, so the two agree bit for bit. */
+void oracle_local_field_nb(const double nb[18], const double Jb[6], double h[3]) {
+  h[0] = h[1] = h[2] = 0.0;
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < 3; ++a) h[a] += Jb[2 * d] * nb[3 * (2 * d) + a] + Jb[2 * d + 1] * nb[3 * (2 * d + 1) + a];
 }
 
 /* Total energy, Eq. 1 with each bond counted once (reading R1). */

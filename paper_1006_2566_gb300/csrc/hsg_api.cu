@@ -672,6 +672,32 @@ hsg_status hsg_set_spins(hsg_ctx* c, const float* in, int where) {
   return HSG_OK;
 }
 
+hsg_status hsg_get_sites(hsg_ctx* c, const uint32_t* sites, int n, float* spins, float* bonds) {
+  if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  if (n < 0) return fail(c, HSG_EINVAL, "n must be >= 0");
+  if (n == 0) return HSG_OK;
+  if (!sites || !spins) return fail(c, HSG_EINVAL, "sites and spins must not be NULL");
+  if (bonds && !c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
+  for (int k = 0; k < n; ++k)
+    if ((long long)sites[k] >= c->N) return fail(c, HSG_EINVAL, "site index out of range");
+  const size_t nb = (size_t)n;
+  hsg_status st = ensure_stage(c, nb * (4 + 12 + 12));
+  if (st != HSG_OK) return st;
+  uint32_t* d_sites = static_cast<uint32_t*>(c->stage);
+  float* d_spins = reinterpret_cast<float*>(d_sites + nb);
+  float* d_bonds = d_spins + 3 * nb;
+  cudaError_t e = cudaMemcpyAsync(d_sites, sites, 4 * nb, cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "site list upload");
+  st = launch(c, HSG_PROF_LAYOUT, 1, "site gather kernel",
+              [&] { return hsg::launch_gather_sites(c->spins, c->J, c->L, d_sites, n, d_spins, d_bonds, c->stream); });
+  if (st != HSG_OK) return st;
+  e = cudaMemcpyAsync(spins, d_spins, 12 * nb, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess && bonds) e = cudaMemcpyAsync(bonds, d_bonds, 12 * nb, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "site readback");
+  return HSG_OK;
+}
+
 hsg_status hsg_get_sweep(hsg_ctx* c, uint64_t* sweep) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
   if (!sweep) return fail(c, HSG_EINVAL, "sweep is NULL");

@@ -112,6 +112,25 @@ __global__ void k_gather_spins(const float4* __restrict__ S, float* __restrict__
   dst[3 * i + 2] = v.z;
 }
 
+// Spins and +d bonds of listed sites (site-major indices i < N): out[3k + a]
+// = component a of site sites[k], bonds[3k + d] = J of its bond to +e_d.
+__global__ void k_gather_sites(const float4* __restrict__ S, const float* __restrict__ J, int L,
+                               const uint32_t* __restrict__ sites, int n, float* __restrict__ spins,
+                               float* __restrict__ bonds) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const uint32_t Lu = (uint32_t)L, Lh = Lu / 2, i = sites[k];
+  const uint32_t x = i % Lu, y = (i / Lu) % Lu, z = i / (Lu * Lu);
+  const uint32_t c = (x + y + z) & 1u;
+  const size_t nh = (size_t)Lu * Lu * Lh;
+  const size_t q = ((size_t)z * Lu + y) * Lh + (x >> 1);
+  const float4 v = S[c * nh + q];
+  spins[3 * (size_t)k] = v.x;
+  spins[3 * (size_t)k + 1] = v.y;
+  spins[3 * (size_t)k + 2] = v.z;
+  for (int d = 0; d < 3; ++d) bonds[3 * (size_t)k + d] = J[(2 * d + c) * nh + q];
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -237,6 +256,13 @@ cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_
 
 cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s) {
   k_gather_spins<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(S, dst, L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_sites(const float4* S, const float* J, int L, const uint32_t* sites, int n, float* spins,
+                                float* bonds, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_gather_sites<<<cdiv(n, 256), 256, 0, s>>>(S, J, L, sites, n, spins, bonds);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,11 @@ cudaError_t launch_gather_couplings(const float* J, float* dst, int L, cudaStrea
 cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_t s);
 cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s);
 
+// Spins (3 per site) and +x/+y/+z bonds of n listed site-major indices
+// (device arrays).  One launch (none for n = 0).
+cudaError_t launch_gather_sites(const float4* S, const float* J, int L, const uint32_t* sites, int n, float* spins,
+                                float* bonds, cudaStream_t s);
+
 // Energy: number of FP64 partial sums the first pass writes, and the
 // two-pass E/N into *out (device).  Two launches.
 // With log_idx set, E/N goes to out[*log_idx] and *log_idx is incremented

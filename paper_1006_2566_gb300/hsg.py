@@ -75,6 +75,7 @@ _SIGS = {
     "hsg_get_spins": ([_vp, _vp, _i], _i),
     "hsg_set_spins": ([_vp, _vp, _i], _i),
     "hsg_get_sweep": ([_vp, ctypes.POINTER(_u64)], _i),
+    "hsg_get_sites": ([_vp, _vp, _i, _vp, _vp], _i),
     "hsg_set_sweep": ([_vp, _u64], _i),
     "hsg_half_sweep": ([_vp, _sch_p, _i, _i], _i),
     "hsg_renorm": ([_vp], _i),
@@ -231,6 +232,17 @@ def hsg_half_sweep(ctx, sched: hsg_schedule, update: int, colour: int) -> None:
 
 def hsg_renorm(ctx) -> None:
     _check(_lib.hsg_renorm(ctx), ctx)
+
+
+def hsg_get_sites(ctx, sites, want_bonds: bool = True):
+    """Spins (n, 3) and, if asked, +x/+y/+z bonds (n, 3) of site-major indices."""
+    idx = np.ascontiguousarray(np.asarray(sites, dtype=np.uint32).reshape(-1))
+    n = idx.size
+    spins = np.empty((n, 3), dtype=np.float32)
+    bonds = np.empty((n, 3), dtype=np.float32) if want_bonds else None
+    _check(_lib.hsg_get_sites(ctx, idx.ctypes.data, n, spins.ctypes.data,
+                              bonds.ctypes.data if want_bonds else None), ctx)
+    return spins, bonds
 
 
 def hsg_kernel_for(ctx, sched: hsg_schedule) -> int:

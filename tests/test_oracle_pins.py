@@ -191,6 +191,40 @@ def test_local_field_of_single_bond(orc):
     assert np.all(orc.local_field(L, J, s, c) == 0.0)
 
 
+def test_per_site_generators_are_the_lattice_generators(orc):
+    """init_spin_sites / gaussian_coupling_sites (any lattice size, for
+    samples) give exactly what the whole-lattice generators give."""
+    L = 6
+    sites = np.random.default_rng(7).permutation(L ** 3)[:100]
+    s = orc.init_spins(L, 9, 2, 1)
+    J = orc.gaussian_couplings(L, 9, 2)
+    assert np.array_equal(orc.init_spin_sites(sites, 9, 2, 1), s.reshape(-1, 3)[sites])
+    assert np.array_equal(orc.gaussian_coupling_sites(sites, 9, 2), J.reshape(-1, 3)[sites])
+
+
+def test_local_field_from_explicit_neighbours_is_the_lattice_field(orc):
+    """local_field_nb (six neighbours and bonds handed over) equals
+    local_field on the whole lattice bit for bit, at every site of an L = 6
+    lattice including the periodic wrap; a neighbour or bond in the wrong
+    slot changes it."""
+    L = 6
+    J = inputs.gaussian_couplings(L, seed=31)
+    s = inputs.random_spins(L, seed=32)
+    for i in range(L ** 3):
+        x, y, z = i % L, (i // L) % L, i // (L * L)
+        nbs, bonds = [], []
+        for d, (dx, dy, dz) in enumerate([(1, 0, 0), (0, 1, 0), (0, 0, 1)]):
+            up = site(L, (x + dx) % L, (y + dy) % L, (z + dz) % L)
+            dn = site(L, (x - dx) % L, (y - dy) % L, (z - dz) % L)
+            nbs += [s[3 * up: 3 * up + 3], s[3 * dn: 3 * dn + 3]]
+            bonds += [J[3 * i + d], J[3 * dn + d]]
+        h = orc.local_field_nb(np.array(nbs), np.array(bonds))
+        assert np.array_equal(h, orc.local_field(L, J, s, i))
+        swapped = list(bonds)
+        swapped[0], swapped[1] = swapped[1], swapped[0]
+        assert not np.allclose(orc.local_field_nb(np.array(nbs), np.array(swapped)), h)
+
+
 # --------------------------------------------------------------------------
 # Over-relaxation (Sec. 4)
 # --------------------------------------------------------------------------
