@@ -27,13 +27,14 @@ KIND_INIT, KIND_JGEN, KIND_MET, KIND_HB = 1, 2, 3, 4
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, no target flags)."""
+    """Compile the oracle with gcc (no FMA contraction, no target flags);
+    with OpenMP where the compiler has it (only the timed CPU baseline uses
+    more than one thread; results do not depend on the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(
-            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"],
-            check=True,
-        )
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.run(base, check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -94,10 +95,22 @@ def _load():
         lib.oracle_half_sweep_range.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                                 ctypes.POINTER(_Params), ctypes.c_int64, ctypes.c_int64, _dp]
         lib.oracle_renorm.argtypes = [ctypes.c_int, _dp]
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_max_threads.restype = ctypes.c_int
         lib.oracle_sweeps.argtypes = [ctypes.c_int, _dp, _dp, ctypes.POINTER(_Schedule), _u32p, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_uint64), _dp, ctypes.POINTER(ctypes.c_int)]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the half-sweep loops (1 by default)."""
+    _load().oracle_set_threads(int(n))
+
+
+def max_threads() -> int:
+    """Processors the OpenMP build can use (1 without OpenMP)."""
+    return int(_load().oracle_max_threads())
 
 
 def _d(a: np.ndarray):

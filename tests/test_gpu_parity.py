@@ -546,6 +546,22 @@ def test_error_paths_on_device(hsg):
         assert lat.sweep_count == 0
         with pytest.raises(hsg.HsgError):
             lat.half_sweep(hsg.schedule(), hsg.HSG_OVERRELAX, 2)
+        # sampled reads and the kernel query
+        for bad_sites in ([8 ** 3], [0, 2 ** 32 - 1]):
+            with pytest.raises(hsg.HsgError) as e:
+                hsg.hsg_get_sites(lat.ctx, np.array(bad_sites, dtype=np.uint64).astype(np.uint32))
+            assert e.value.status == hsg.HSG_EINVAL
+        spins, bonds = hsg.hsg_get_sites(lat.ctx, np.array([], dtype=np.uint32))
+        assert spins.shape == (0, 3) and bonds.shape == (0, 3)
+        with pytest.raises(hsg.HsgError) as e:
+            hsg.hsg_kernel_for(lat.ctx, hsg.schedule(kernel=9))
+        assert e.value.status == hsg.HSG_EINVAL
+    with hsg.Lattice(8, 1) as fresh:  # bonds before couplings are set
+        with pytest.raises(hsg.HsgError) as e:
+            hsg.hsg_get_sites(fresh.ctx, np.array([0], dtype=np.uint32))
+        assert e.value.status == hsg.HSG_EINVAL
+        s, b = hsg.hsg_get_sites(fresh.ctx, np.array([0, 511], dtype=np.uint32), want_bonds=False)
+        assert b is None and np.array_equal(s, fresh.spins().reshape(-1, 3)[[0, 511]])
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4, 5])

@@ -191,6 +191,27 @@ def test_local_field_of_single_bond(orc):
     assert np.all(orc.local_field(L, J, s, c) == 0.0)
 
 
+def test_half_sweeps_do_not_depend_on_the_thread_count(orc):
+    """The OpenMP loop of a half-sweep (used to time the CPU baseline on all
+    cores) gives the same state and margins as one thread."""
+    L = 10
+    J = inputs.gaussian_couplings(L, seed=41)
+    p = orc.Params(key=orc.key(41), sweep=3, beta=1.5, hits=3, proposal=orc.PROP_BALL)
+    outs = []
+    for threads in (1, max(2, orc.max_threads())):
+        orc.set_threads(threads)
+        try:
+            s = orc.init_spins(L, 41)
+            m = [orc.half_sweep(L, J, s, upd, c, p, want_margins=True) for upd in (orc.MET, orc.HB, orc.OR)
+                 for c in (0, 1)]
+        finally:
+            orc.set_threads(1)
+        outs.append((s, m))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        assert np.array_equal(a, b, equal_nan=True)
+
+
 def test_per_site_generators_are_the_lattice_generators(orc):
     """init_spin_sites / gaussian_coupling_sites (any lattice size, for
     samples) give exactly what the whole-lattice generators give."""
