@@ -47,6 +47,9 @@ BYTES_OR, BYTES_HB, BYTES_ENERGY, BYTES_RENORM = 72, 56, 28, 32
 # Temporally blocked over-relaxation sweep (both colours in one pass), per
 # site update: all spins read 16 + written 16, all bonds 12.
 BYTES_OR_WAVE = 44
+# Packed layout (12-byte spins): OR 12 r + 12 w + 12 + 24, heat-bath 12 w + 12
+# + 24, energy 12 + 12, renormalisation 12 r + 12 w.
+BYTES_OR_PACKED, BYTES_HB_PACKED, BYTES_ENERGY_PACKED, BYTES_RENORM_PACKED = 60, 48, 24, 24
 
 WORKLOADS = {
     "l256_hb_or": dict(
@@ -91,6 +94,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serving"], default="l256_hb_or")
     ap.add_argument("--kernel", choices=["auto", "global", "slab", "wave"], default="auto")
+    ap.add_argument("--layout", choices=["float4", "packed"], default="float4", help="device spin layout")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
@@ -191,7 +195,8 @@ def kernel_source_hash() -> str:
 def profiled_traffic(kernel_variant: str, L: int):
     """DRAM bytes per over-relaxation launch from the committed ncu summary,
     if it was taken on the current kernel source; else None."""
-    name = f"or_full_sweep_wave_L{L}.md" if kernel_variant == "wave" else f"or_half_sweep_{kernel_variant}_L{L}.md"
+    name = {"wave": f"or_full_sweep_wave_L{L}.md", "packed": f"or_half_sweep_packed_L{L}.md"}.get(
+        kernel_variant, f"or_half_sweep_{kernel_variant}_L{L}.md")
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -209,16 +214,18 @@ def step_units(wl) -> int:
     return (wl["L"] ** 3) * passes * wl["sweeps_per_step"]
 
 
-def step_bytes(wl, wave: bool = False) -> int:
+def step_bytes(wl, wave: bool = False, packed: bool = False) -> int:
     n = wl["L"] ** 3
-    main = {"HB": BYTES_HB, "MET": BYTES_OR, "METOR": BYTES_OR}.get(wl["kind"], 0)
-    per_sweep = n * (main + wl["n_or"] * (BYTES_OR_WAVE if wave else BYTES_OR))
+    b_or, b_hb = (BYTES_OR_PACKED, BYTES_HB_PACKED) if packed else (BYTES_OR, BYTES_HB)
+    b_en, b_rn = (BYTES_ENERGY_PACKED, BYTES_RENORM_PACKED) if packed else (BYTES_ENERGY, BYTES_RENORM)
+    main = {"HB": b_hb, "MET": b_or, "METOR": b_or}.get(wl["kind"], 0)
+    per_sweep = n * (main + wl["n_or"] * (BYTES_OR_WAVE if wave else b_or))
     s = wl["sweeps_per_step"]
     extra = 0
     if wl["energy_every"]:
-        extra += n * BYTES_ENERGY * (s // wl["energy_every"])
+        extra += n * b_en * (s // wl["energy_every"])
     if wl["renorm_every"]:
-        extra += n * BYTES_RENORM * (s // wl["renorm_every"])
+        extra += n * b_rn * (s // wl["renorm_every"])
     return per_sweep * s + extra
 
 
@@ -257,7 +264,9 @@ def run_ours(args, wl):
     stream = torch.cuda.Stream()
     sample = hdist.rank_sample(rank)  # weak scaling: one disorder sample per rank
     J = inputs.gaussian_couplings(L, seed=wl["seed"], sample=sample, dtype=np.float32)
-    lat = hsg.Lattice(L, wl["seed"], sample, 0, stream)
+    packed = args.layout == "packed"
+    lat = hsg.Lattice(L, wl["seed"], sample, 0, stream,
+                      layout=hsg.HSG_LAYOUT_PACKED if packed else hsg.HSG_LAYOUT_FLOAT4)
     lat.set_couplings(J)
     kernel_used = hsg.hsg_kernel_for(lat.ctx, sched)  # what HSG_KERNEL_AUTO resolves to
     # inputs resident in HBM from here on
@@ -349,16 +358,20 @@ def run_ours(args, wl):
     variant = {hsg.HSG_KERNEL_GLOBAL: "global", hsg.HSG_KERNEL_SLAB: "slab",
                hsg.HSG_KERNEL_WAVE: "wave"}[kernel_used]
     wave = variant == "wave"
+    if packed:
+        variant = "packed"  # the global kernel over the packed layout
     # Units one over-relaxation launch processes: N/2 sites per half-sweep,
     # N per wave sweep.
     units = N if wave else nh
-    b_or = BYTES_OR_WAVE if wave else BYTES_OR
+    b_or = BYTES_OR_WAVE if wave else (BYTES_OR_PACKED if packed else BYTES_OR)
+    b_hb = BYTES_HB_PACKED if packed else BYTES_HB
     roof = None
     if or_n:
         alg = units * b_or
         avg_s = or_ms / or_n / 1e3
         ach = alg / avg_s / 1e9
-        kname = "over-relaxation full sweep, temporally blocked" if wave else "over-relaxation half-sweep"
+        kname = ("over-relaxation full sweep, temporally blocked" if wave else
+                 "over-relaxation half-sweep, packed spins" if packed else "over-relaxation half-sweep")
         roof = {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
                 "traffic": profiled_traffic(variant, L), "algorithmic_bytes_per_launch": alg,
@@ -369,33 +382,35 @@ def run_ours(args, wl):
                 "single_pass_equivalent": ({"bytes_per_update": BYTES_OR,
                                             "GBps": round(units * BYTES_OR / avg_s / 1e9, 1),
                                             "frac": round(units * BYTES_OR / avg_s / 1e9 / peak, 4)}
-                                           if wave else None),
+                                           if wave or packed else None),
                 "measured_over": f"{args.steps} steps with per-launch CUDA events ({profiled_ms / args.steps:.3f} "
                                  f"ms/step, directly launched)"}
     kernels = {}
-    for name, (ms, n), bpu, u in (("heatbath", (hb_ms, hb_n), BYTES_HB, nh), ("overrelax", (or_ms, or_n), b_or, units),
-                                  ("metropolis", (met_ms, met_n), BYTES_OR, nh)):
+    for name, (ms, n), bpu, u in (("heatbath", (hb_ms, hb_n), b_hb, nh), ("overrelax", (or_ms, or_n), b_or, units),
+                                  ("metropolis", (met_ms, met_n), BYTES_OR_PACKED if packed else BYTES_OR, nh)):
         if n:
             kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
                              "GBps": round(u * bpu / (ms / n / 1e3) / 1e9, 1)}
     for name, k in (("energy", hsg.HSG_PROF_ENERGY), ("renorm", hsg.HSG_PROF_RENORM)):
         ms, n = per_class[k]
         if n:
-            bpu = BYTES_ENERGY if name == "energy" else BYTES_RENORM
+            bpu = ((BYTES_ENERGY_PACKED if packed else BYTES_ENERGY) if name == "energy" else
+                   (BYTES_RENORM_PACKED if packed else BYTES_RENORM))
             kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
                              "GBps": round(N * bpu / (ms / n / 1e3) / 1e9, 1)}
-    step_gbps = step_bytes(wl, wave) / (elapsed_ms / args.steps / 1e3) / 1e9
+    step_gbps = step_bytes(wl, wave, packed) / (elapsed_ms / args.steps / 1e3) / 1e9
     out = {
         "metric": "spin updates/ns", "value": round(value, 4), "unit": "spin updates/ns", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: seeded Gaussian J (numpy), spins uniform on S^2 from Philox",
         "config": {"workload": wl["desc"], "L": L, "sweeps_per_step": sps, "kernel": variant,
+                   "spin_layout": "packed (3 fp32 arrays per colour)" if packed else "float4",
                    "parallelism": f"samples{world}" if world > 1 else "single sample",
                    "l2": "inputs larger than L2 (state 470 MB vs 126 MB L2), no flush" if L >= 256 else
                          "state fits in L2"},
         "roofline": roof,
-        "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes(wl, wave),
+        "step_roofline": {"bound": "hbm", "algorithmic_bytes_per_step": step_bytes(wl, wave, packed),
                           "achieved_GBps": round(step_gbps, 1), "frac": round(step_gbps / peak, 4)},
         "kernels": kernels,
         "gpu_launches": int(launches),

@@ -90,6 +90,13 @@ enum {
   HSG_KERNEL_WAVE = 3
 };
 
+/* Device layout of the spins (hsg_create_layout). */
+enum {
+  HSG_LAYOUT_FLOAT4 = 0, /* one float4 per spin (16 bytes: x, y, z, unused) */
+  HSG_LAYOUT_PACKED = 1  /* three fp32 arrays per colour (12 bytes a spin): 60 instead of 72
+                          * bytes per over-relaxation update; global kernel only */
+};
+
 /* Kernel classes reported by the profiler. */
 enum {
   HSG_PROF_INIT = 0,
@@ -148,6 +155,19 @@ typedef struct hsg_ctx hsg_ctx; /* opaque, library-owned */
  */
 hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica,
                       void* cuda_stream);
+
+/*
+ * hsg_create with a choice of device spin layout.  HSG_LAYOUT_PACKED keeps
+ * each colour as three fp32 component arrays instead of float4: the paper's
+ * own footprint of six single-precision words per lattice point, three spin
+ * components and three bonds (Sec. 4), 25 % fewer spin bytes per update than
+ * float4, the same results bit for bit.  A packed
+ * lattice sweeps with the global kernel (HSG_KERNEL_AUTO or _GLOBAL;
+ * _SLAB / _WAVE return HSG_EINVAL).  Library-specific (the paper has one
+ * layout).  Errors as hsg_create, and HSG_EINVAL for an unknown layout.
+ */
+hsg_status hsg_create_layout(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica,
+                             void* cuda_stream, int layout);
 
 /* Release everything the context owns; waits for its stream.  NULL is a
  * no-op returning HSG_OK. */

@@ -45,7 +45,8 @@ struct hsg_ctx {
   cudaStream_t stream = nullptr;
   int device = 0, sm_count = 0;
   long long l2_bytes = 0;  // the device's L2 size
-  float4* spins = nullptr;      // [2][Nh], the current state
+  bool packed = false;          // spin layout: three fp32 arrays per colour instead of float4
+  float4* spins = nullptr;      // [2][Nh] float4 (or [2][3][Nh] floats, packed), the current state
   float4* spins_alt = nullptr;  // [2][Nh], target of the temporally blocked sweeps (allocated on first use)
   float* J = nullptr;       // [3][2][Nh]
   bool have_J = false;
@@ -214,6 +215,13 @@ hsg::SweepArgs sweep_args(hsg_ctx* c, int colour, float beta, float step, int hi
   a.beta = beta;
   a.step = step;
   a.sweep_ptr = c->d_ctr;  // the device counter equals c->sweep in stream order
+  if (c->packed) {
+    float* base = reinterpret_cast<float*>(c->spins);
+    a.own = reinterpret_cast<float4*>(base + 3 * colour * c->Nh);
+    a.oth = reinterpret_cast<const float4*>(base + 3 * o * c->Nh);
+    a.packed = true;
+    a.stride = (size_t)c->Nh;
+  }
   return a;
 }
 
@@ -232,6 +240,8 @@ hsg_status check_schedule(hsg_ctx* c, const hsg_schedule* s, bool need_kind) {
   if (s->kernel != HSG_KERNEL_AUTO && s->kernel != HSG_KERNEL_GLOBAL && s->kernel != HSG_KERNEL_SLAB &&
       s->kernel != HSG_KERNEL_WAVE)
     return fail(c, HSG_EINVAL, "schedule.kernel must be HSG_KERNEL_AUTO, _GLOBAL, _SLAB or _WAVE");
+  if (c->packed && (s->kernel == HSG_KERNEL_SLAB || s->kernel == HSG_KERNEL_WAVE))
+    return fail(c, HSG_EINVAL, "the packed spin layout runs the global kernel only (HSG_KERNEL_AUTO or _GLOBAL)");
   return HSG_OK;
 }
 
@@ -244,6 +254,7 @@ float beta_of(double T) { return std::isinf(T) ? 0.0f : (float)(1.0 / T); }
 // whose 59 MB state stays in the 126 MB L2).
 int pick_variant(const hsg_ctx* c, int requested) {
   if (requested == HSG_KERNEL_GLOBAL || requested == HSG_KERNEL_SLAB || requested == HSG_KERNEL_WAVE) return requested;
+  if (c->packed) return hsg::V_GLOBAL;
   return 28LL * c->N > c->l2_bytes ? hsg::V_WAVE : hsg::V_GLOBAL;
 }
 
@@ -292,7 +303,7 @@ hsg_status run_or_sweep_wave(hsg_ctx* c) {
 hsg_status run_energy(hsg_ctx* c, double* out_dev, bool logged) {
   unsigned long long* idx = logged ? c->d_ctr + 1 : nullptr;
   return launch(c, HSG_PROF_ENERGY, 2, "energy kernels",
-                [&] { return hsg::launch_energy(c->spins, c->J, c->L, c->partials, out_dev, idx, c->stream); });
+                [&] { return hsg::launch_energy(c->spins, c->packed, c->J, c->L, c->partials, out_dev, idx, c->stream); });
 }
 
 hsg_status run_advance(hsg_ctx* c) {
@@ -301,7 +312,7 @@ hsg_status run_advance(hsg_ctx* c) {
 
 hsg_status run_renorm(hsg_ctx* c) {
   return launch(c, HSG_PROF_RENORM, 1, "renorm kernel",
-                [&] { return hsg::launch_renorm(c->spins, c->N, c->sm_count, c->stream); });
+                [&] { return hsg::launch_renorm(c->spins, c->packed, c->N, c->sm_count, c->stream); });
 }
 
 // One sweep's launches in schedule order; the host mirrors of the sweep
@@ -405,12 +416,20 @@ void hsg::set_thread_error(const std::string& msg) { g_thread_error = msg; }
 extern "C" {
 
 hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica, void* cuda_stream) {
+  return hsg_create_layout(out, L, seed, sample, replica, cuda_stream, HSG_LAYOUT_FLOAT4);
+}
+
+hsg_status hsg_create_layout(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica,
+                             void* cuda_stream, int layout) {
   if (!out) return fail(nullptr, HSG_EINVAL, "out is NULL");
   *out = nullptr;
   if (L < 4 || L > kMaxL || (L & 1))
     return fail(nullptr, HSG_EINVAL, "L must be even and in [4, " + std::to_string(kMaxL) + "]");
+  if (layout != HSG_LAYOUT_FLOAT4 && layout != HSG_LAYOUT_PACKED)
+    return fail(nullptr, HSG_EINVAL, "layout must be HSG_LAYOUT_FLOAT4 or HSG_LAYOUT_PACKED");
   hsg_ctx* c = new (std::nothrow) hsg_ctx();
   if (!c) return fail(nullptr, HSG_ENOMEM, "host allocation failed");
+  c->packed = layout == HSG_LAYOUT_PACKED;
   c->L = L;
   c->Lh = L / 2;
   c->N = (long long)L * L * L;
@@ -438,7 +457,7 @@ hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint
     size_t bytes;
     const char* what;
   } allocs[] = {
-      {reinterpret_cast<void**>(&c->spins), sizeof(float4) * (size_t)c->N, "spins"},
+      {reinterpret_cast<void**>(&c->spins), (c->packed ? 3 * sizeof(float) : sizeof(float4)) * (size_t)c->N, "spins"},
       {reinterpret_cast<void**>(&c->J), sizeof(float) * 3 * (size_t)c->N, "couplings"},
       {reinterpret_cast<void**>(&c->partials), sizeof(double) * hsg::energy_partials(L), "energy partials"},
       {reinterpret_cast<void**>(&c->e_out), sizeof(double), "energy result"},
@@ -467,7 +486,7 @@ hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint
     return st;
   }
   st = launch(c, HSG_PROF_INIT, 1, "init kernel",
-              [&] { return hsg::launch_init_spins(c->spins, L, c->k0, c->k1, c->stream); });
+              [&] { return hsg::launch_init_spins(c->spins, c->packed, L, c->k0, c->k1, c->stream); });
   if (st != HSG_OK) {
     g_thread_error = c->err;
     release(c);
@@ -639,7 +658,7 @@ hsg_status hsg_get_spins(hsg_ctx* c, float* out, int where) {
     dst = static_cast<float*>(c->stage);
   }
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "spin gather kernel",
-                         [&] { return hsg::launch_gather_spins(c->spins, dst, c->L, c->stream); });
+                         [&] { return hsg::launch_gather_spins(c->spins, c->packed, dst, c->L, c->stream); });
   if (st != HSG_OK) return st;
   if (where == HSG_HOST) {
     cudaError_t e = cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream);
@@ -663,7 +682,7 @@ hsg_status hsg_set_spins(hsg_ctx* c, const float* in, int where) {
     src = static_cast<const float*>(c->stage);
   }
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "spin scatter kernel",
-                         [&] { return hsg::launch_scatter_spins(src, c->spins, c->L, c->stream); });
+                         [&] { return hsg::launch_scatter_spins(src, c->spins, c->packed, c->L, c->stream); });
   if (st != HSG_OK) return st;
   if (where == HSG_HOST) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -689,7 +708,10 @@ hsg_status hsg_get_sites(hsg_ctx* c, const uint32_t* sites, int n, float* spins,
   cudaError_t e = cudaMemcpyAsync(d_sites, sites, 4 * nb, cudaMemcpyHostToDevice, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "site list upload");
   st = launch(c, HSG_PROF_LAYOUT, 1, "site gather kernel",
-              [&] { return hsg::launch_gather_sites(c->spins, c->J, c->L, d_sites, n, d_spins, d_bonds, c->stream); });
+              [&] {
+                return hsg::launch_gather_sites(c->spins, c->packed, c->J, c->L, d_sites, n, d_spins, d_bonds,
+                                                c->stream);
+              });
   if (st != HSG_OK) return st;
   e = cudaMemcpyAsync(spins, d_spins, 12 * nb, cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess && bonds) e = cudaMemcpyAsync(bonds, d_bonds, 12 * nb, cudaMemcpyDeviceToHost, c->stream);

@@ -9,13 +9,37 @@ namespace {
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
+// Spin (c, q) of a lattice in either layout (hsg_device.cuh): float4
+// S[c][N/2], or packed float S[c][a][N/2].
+template <bool PACKED>
+__device__ __forceinline__ float4 spin_get(const void* S, long long nh, int c, long long q) {
+  if constexpr (PACKED) {
+    const float* b = static_cast<const float*>(S) + 3 * c * nh + q;
+    return make_float4(__ldg(b), __ldg(b + nh), __ldg(b + 2 * nh), 0.0f);
+  } else {
+    return __ldg(static_cast<const float4*>(S) + c * nh + q);
+  }
+}
+template <bool PACKED>
+__device__ __forceinline__ void spin_put(void* S, long long nh, int c, long long q, float4 v) {
+  if constexpr (PACKED) {
+    float* b = static_cast<float*>(S) + 3 * c * nh + q;
+    b[0] = v.x;
+    b[nh] = v.y;
+    b[2 * nh] = v.z;
+  } else {
+    static_cast<float4*>(S)[c * nh + q] = v;
+  }
+}
+
 constexpr int ENERGY_THREADS = 256;
 constexpr int ENERGY_BLOCKS = 1024;  // fixed, so the summation order is fixed
 constexpr int FINAL_THREADS = 1024;
 
 // Spin initialisation: site i gets the sphere point of Philox counter
 // (i, 0, INIT<<24, 0).  Grid (Lh/32, L/8, 2L): blockIdx.z = 2 z + colour.
-__global__ void k_init_spins(float4* __restrict__ S, int L, uint32_t k0, uint32_t k1) {
+template <bool PACKED>
+__global__ void k_init_spins(void* __restrict__ S, int L, uint32_t k0, uint32_t k1) {
   const int Lh = L / 2;
   const int xh = blockIdx.x * 32 + threadIdx.x;
   const int y = blockIdx.y * 8 + threadIdx.y;
@@ -26,7 +50,7 @@ __global__ void k_init_spins(float4* __restrict__ S, int L, uint32_t k0, uint32_
   const uint4 r = philox4x32_10(make_uint4(site, 0u, KIND_INIT << 24, 0u), k0, k1);
   const float3 v = sphere_point(u01(r.x), u01(r.y));
   const long long nh = (long long)L * L * Lh;
-  S[c * nh + ((long long)z * L + y) * Lh + xh] = make_float4(v.x, v.y, v.z, 0.0f);
+  spin_put<PACKED>(S, nh, c, ((long long)z * L + y) * Lh + xh, make_float4(v.x, v.y, v.z, 0.0f));
 }
 
 // Site-major -> colour-split couplings.  Thread per site (x, y, z).
@@ -85,7 +109,8 @@ __global__ void k_gather_couplings(const float* __restrict__ J, float* __restric
   for (int d = 0; d < 3; ++d) dst[3 * i + d] = J[(2 * d + c) * nh + q];
 }
 
-__global__ void k_scatter_spins(const float* __restrict__ src, float4* __restrict__ S, int L) {
+template <bool PACKED>
+__global__ void k_scatter_spins(const float* __restrict__ src, void* __restrict__ S, int L) {
   const int x = blockIdx.x * 64 + threadIdx.x;
   const int y = blockIdx.y * 4 + threadIdx.y;
   const int z = blockIdx.z;
@@ -94,10 +119,12 @@ __global__ void k_scatter_spins(const float* __restrict__ src, float4* __restric
   const long long nh = (long long)L * L * Lh;
   const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
   const int c = (x + y + z) & 1;
-  S[c * nh + ((long long)z * L + y) * Lh + (x >> 1)] = make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0f);
+  spin_put<PACKED>(S, nh, c, ((long long)z * L + y) * Lh + (x >> 1),
+                   make_float4(src[3 * i], src[3 * i + 1], src[3 * i + 2], 0.0f));
 }
 
-__global__ void k_gather_spins(const float4* __restrict__ S, float* __restrict__ dst, int L) {
+template <bool PACKED>
+__global__ void k_gather_spins(const void* __restrict__ S, float* __restrict__ dst, int L) {
   const int x = blockIdx.x * 64 + threadIdx.x;
   const int y = blockIdx.y * 4 + threadIdx.y;
   const int z = blockIdx.z;
@@ -106,7 +133,7 @@ __global__ void k_gather_spins(const float4* __restrict__ S, float* __restrict__
   const long long nh = (long long)L * L * Lh;
   const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
   const int c = (x + y + z) & 1;
-  const float4 v = S[c * nh + ((long long)z * L + y) * Lh + (x >> 1)];
+  const float4 v = spin_get<PACKED>(S, nh, c, ((long long)z * L + y) * Lh + (x >> 1));
   dst[3 * i] = v.x;
   dst[3 * i + 1] = v.y;
   dst[3 * i + 2] = v.z;
@@ -114,7 +141,8 @@ __global__ void k_gather_spins(const float4* __restrict__ S, float* __restrict__
 
 // Spins and +d bonds of listed sites (site-major indices i < N): out[3k + a]
 // = component a of site sites[k], bonds[3k + d] = J of its bond to +e_d.
-__global__ void k_gather_sites(const float4* __restrict__ S, const float* __restrict__ J, int L,
+template <bool PACKED>
+__global__ void k_gather_sites(const void* __restrict__ S, const float* __restrict__ J, int L,
                                const uint32_t* __restrict__ sites, int n, float* __restrict__ spins,
                                float* __restrict__ bonds) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -124,7 +152,7 @@ __global__ void k_gather_sites(const float4* __restrict__ S, const float* __rest
   const uint32_t c = (x + y + z) & 1u;
   const size_t nh = (size_t)Lu * Lu * Lh;
   const size_t q = ((size_t)z * Lu + y) * Lh + (x >> 1);
-  const float4 v = S[c * nh + q];
+  const float4 v = spin_get<PACKED>(S, (long long)nh, (int)c, (long long)q);
   spins[3 * (size_t)k] = v.x;
   spins[3 * (size_t)k + 1] = v.y;
   spins[3 * (size_t)k + 2] = v.z;
@@ -142,13 +170,12 @@ __device__ __forceinline__ double warp_sum(double v) {
 // local field of Eq. 2.  The site term s_i . h_i is formed in FP32 (as in
 // the updates, relative error a few ulp); every sum over sites is FP64.
 // Block b writes partials[b].
-__global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const float4* __restrict__ S,
+template <bool PACKED>
+__global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const void* __restrict__ S,
                                                                    const float* __restrict__ J, int L,
                                                                    double* __restrict__ partials) {
   const uint32_t Lh = (uint32_t)L / 2;
   const uint32_t nh = (uint32_t)L * (uint32_t)L * Lh;
-  const float4* s0 = S;
-  const float4* s1 = S + nh;
   const float *jx0 = J, *jx1 = J + nh, *jy0 = J + 2ull * nh, *jy1 = J + 3ull * nh, *jz0 = J + 4ull * nh,
               *jz1 = J + 5ull * nh;
   double acc = 0.0;
@@ -164,10 +191,12 @@ __global__ void __launch_bounds__(ENERGY_THREADS) k_energy_partial(const float4*
     const long long q_ym = ((long long)z * L + wrap_dec(y, L)) * Lh + xh;
     const long long q_zp = ((long long)wrap_inc(z, L) * L + y) * Lh + xh;
     const long long q_zm = ((long long)wrap_dec(z, L) * L + y) * Lh + xh;
-    const float3 h = local_field(__ldg(s1 + q_xp), __ldg(s1 + q_xm), __ldg(s1 + q_yp), __ldg(s1 + q_ym),
-                                 __ldg(s1 + q_zp), __ldg(s1 + q_zm), __ldg(jx0 + t), __ldg(jx1 + q_xm),
-                                 __ldg(jy0 + t), __ldg(jy1 + q_ym), __ldg(jz0 + t), __ldg(jz1 + q_zm));
-    const float4 s = __ldg(s0 + t);
+    const float3 h = local_field(spin_get<PACKED>(S, nh, 1, q_xp), spin_get<PACKED>(S, nh, 1, q_xm),
+                                 spin_get<PACKED>(S, nh, 1, q_yp), spin_get<PACKED>(S, nh, 1, q_ym),
+                                 spin_get<PACKED>(S, nh, 1, q_zp), spin_get<PACKED>(S, nh, 1, q_zm), __ldg(jx0 + t),
+                                 __ldg(jx1 + q_xm), __ldg(jy0 + t), __ldg(jy1 + q_ym), __ldg(jz0 + t),
+                                 __ldg(jz1 + q_zm));
+    const float4 s = spin_get<PACKED>(S, nh, 0, t);
     acc += (double)dot3(make_float3(s.x, s.y, s.z), h);
   }
   __shared__ double warp_part[ENERGY_THREADS / 32];
@@ -211,10 +240,21 @@ __global__ void __launch_bounds__(FINAL_THREADS) k_energy_final(const double* __
 __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
 __global__ void k_add_u64(unsigned long long* p, unsigned long long d) { *p += d; }
 
-// Renormalisation of every spin (renorm_spin, hsg_device.cuh).
-__global__ void k_renorm(float4* __restrict__ S, long long n) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    S[t] = renorm_spin(S[t]);
+// Renormalisation of every spin (renorm_spin, hsg_device.cuh); n = N sites,
+// t = c * N/2 + q.
+template <bool PACKED>
+__global__ void k_renorm(void* __restrict__ S, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    if constexpr (PACKED) {
+      const long long nh = n / 2;
+      const int c = t >= nh;
+      const long long q = t - c * nh;
+      spin_put<true>(S, nh, c, q, renorm_spin(spin_get<true>(S, nh, c, q)));
+    } else {
+      float4* S4 = static_cast<float4*>(S);
+      S4[t] = renorm_spin(S4[t]);
+    }
+  }
 }
 
 __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n,
@@ -225,8 +265,12 @@ __global__ void k_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uin
 
 }  // namespace
 
-cudaError_t launch_init_spins(float4* S, int L, uint32_t k0, uint32_t k1, cudaStream_t s) {
-  k_init_spins<<<dim3(cdiv(L / 2, 32), cdiv(L, 8), 2u * L), dim3(32, 8), 0, s>>>(S, L, k0, k1);
+cudaError_t launch_init_spins(void* S, bool packed, int L, uint32_t k0, uint32_t k1, cudaStream_t s) {
+  const dim3 grid(cdiv(L / 2, 32), cdiv(L, 8), 2u * L), block(32, 8);
+  if (packed)
+    k_init_spins<true><<<grid, block, 0, s>>>(S, L, k0, k1);
+  else
+    k_init_spins<false><<<grid, block, 0, s>>>(S, L, k0, k1);
   return cudaGetLastError();
 }
 
@@ -249,20 +293,31 @@ cudaError_t launch_gather_couplings(const float* J, float* dst, int L, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_t s) {
-  k_scatter_spins<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(src, S, L);
+cudaError_t launch_scatter_spins(const float* src, void* S, bool packed, int L, cudaStream_t s) {
+  const dim3 grid(cdiv(L, 64), cdiv(L, 4), (unsigned)L), block(64, 4);
+  if (packed)
+    k_scatter_spins<true><<<grid, block, 0, s>>>(src, S, L);
+  else
+    k_scatter_spins<false><<<grid, block, 0, s>>>(src, S, L);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s) {
-  k_gather_spins<<<dim3(cdiv(L, 64), cdiv(L, 4), (unsigned)L), dim3(64, 4), 0, s>>>(S, dst, L);
+cudaError_t launch_gather_spins(const void* S, bool packed, float* dst, int L, cudaStream_t s) {
+  const dim3 grid(cdiv(L, 64), cdiv(L, 4), (unsigned)L), block(64, 4);
+  if (packed)
+    k_gather_spins<true><<<grid, block, 0, s>>>(S, dst, L);
+  else
+    k_gather_spins<false><<<grid, block, 0, s>>>(S, dst, L);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_sites(const float4* S, const float* J, int L, const uint32_t* sites, int n, float* spins,
-                                float* bonds, cudaStream_t s) {
+cudaError_t launch_gather_sites(const void* S, bool packed, const float* J, int L, const uint32_t* sites, int n,
+                                float* spins, float* bonds, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_gather_sites<<<cdiv(n, 256), 256, 0, s>>>(S, J, L, sites, n, spins, bonds);
+  if (packed)
+    k_gather_sites<true><<<cdiv(n, 256), 256, 0, s>>>(S, J, L, sites, n, spins, bonds);
+  else
+    k_gather_sites<false><<<cdiv(n, 256), 256, 0, s>>>(S, J, L, sites, n, spins, bonds);
   return cudaGetLastError();
 }
 
@@ -272,10 +327,13 @@ size_t energy_partials(int L) {
   return (size_t)(b < ENERGY_BLOCKS ? b : ENERGY_BLOCKS);
 }
 
-cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out,
+cudaError_t launch_energy(const void* S, bool packed, const float* J, int L, double* partials, double* out,
                           unsigned long long* log_idx, cudaStream_t s) {
   const int nb = (int)energy_partials(L);
-  k_energy_partial<<<nb, ENERGY_THREADS, 0, s>>>(S, J, L, partials);
+  if (packed)
+    k_energy_partial<true><<<nb, ENERGY_THREADS, 0, s>>>(S, J, L, partials);
+  else
+    k_energy_partial<false><<<nb, ENERGY_THREADS, 0, s>>>(S, J, L, partials);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_energy_final<<<1, FINAL_THREADS, 0, s>>>(partials, nb, 1.0 / ((double)L * L * L), out, log_idx);
@@ -292,10 +350,14 @@ cudaError_t launch_add_u64(unsigned long long* p, unsigned long long d, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_renorm(float4* S, long long n, int sm_count, cudaStream_t s) {
+cudaError_t launch_renorm(void* S, bool packed, long long n, int sm_count, cudaStream_t s) {
   const long long want = (n + 255) / 256;
   const long long cap = (long long)sm_count * 8;
-  k_renorm<<<(unsigned)(want < cap ? want : cap), 256, 0, s>>>(S, n);
+  const unsigned grid = (unsigned)(want < cap ? want : cap);
+  if (packed)
+    k_renorm<true><<<grid, 256, 0, s>>>(S, n);
+  else
+    k_renorm<false><<<grid, 256, 0, s>>>(S, n);
   return cudaGetLastError();
 }
 

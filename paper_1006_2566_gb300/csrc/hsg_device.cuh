@@ -4,7 +4,8 @@
 // Device layout ("colour-split"): colour c of site (x,y,z) is (x+y+z) & 1.
 // With Lh = L/2, the sites of colour c in row (y,z) have x = 2*xh + p,
 // p = (c + y + z) & 1, and are stored at q = (z*L + y)*Lh + xh of
-//   spins  float4 S[c][N/2]            (x, y, z, unused)
+//   spins  float4 S[c][N/2]            (x, y, z, unused), or, packed
+//          float  S[c][a][N/2]         component a = 0,1,2 (12 bytes a spin)
 //   bonds  float  J[d][c][N/2]         d = 0,1,2: bond from the site to +x,+y,+z.
 // A site of colour c finds its six neighbours in colour 1-c at
 //   x+1: xh + p (wrapped)   x-1: xh - 1 + p (wrapped)   in the same row,
@@ -222,6 +223,31 @@ __device__ __forceinline__ float4 renorm_spin(float4 v) {
   return v;
 }
 
+// The spins of one colour: float4 per site, or three component arrays
+// (packed layout).  Both hand the site code the same float4 values, so the
+// arithmetic -- and the result -- is the same in either layout.
+struct SpinsF4 {
+  float4* p;
+  __device__ __forceinline__ float4 ldg(uint32_t q) const { return __ldg(p + q); }
+  __device__ __forceinline__ float4 ld(uint32_t q) const { return p[q]; }
+  __device__ __forceinline__ void st(uint32_t q, float4 v) const { p[q] = v; }
+};
+struct SpinsSoA {
+  float* p;       // component 0; components 1 and 2 at + stride, + 2 stride
+  size_t stride;  // N/2
+  __device__ __forceinline__ float4 ldg(uint32_t q) const {
+    return make_float4(__ldg(p + q), __ldg(p + stride + q), __ldg(p + 2 * stride + q), 0.0f);
+  }
+  __device__ __forceinline__ float4 ld(uint32_t q) const {
+    return make_float4(p[q], p[stride + q], p[2 * stride + q], 0.0f);
+  }
+  __device__ __forceinline__ void st(uint32_t q, float4 v) const {
+    p[q] = v.x;
+    p[stride + q] = v.y;
+    p[2 * stride + q] = v.z;
+  }
+};
+
 // What one site of a half-sweep reads: its six other-colour neighbours and
 // bonds, its own spin, its index q and its Philox site number.
 struct SiteInputs {
@@ -233,13 +259,12 @@ struct SiteInputs {
 
 // Gather the inputs of site (x = 2 xh + p, y, z) of colour `colour` (layout
 // at the top of this file).  Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.
-template <int U>
-__device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __restrict__ own,
-                                            const float4* __restrict__ oth, const float* __restrict__ jx_own,
-                                            const float* __restrict__ jy_own, const float* __restrict__ jz_own,
-                                            const float* __restrict__ jx_oth, const float* __restrict__ jy_oth,
-                                            const float* __restrict__ jz_oth, uint32_t xh, uint32_t y, uint32_t z,
-                                            uint32_t L, uint32_t Lh, uint32_t colour) {
+template <int U, class Spins>
+__device__ __forceinline__ void gather_site_in(SiteInputs& in, Spins own, Spins oth, const float* __restrict__ jx_own,
+                                               const float* __restrict__ jy_own, const float* __restrict__ jz_own,
+                                               const float* __restrict__ jx_oth, const float* __restrict__ jy_oth,
+                                               const float* __restrict__ jz_oth, uint32_t xh, uint32_t y, uint32_t z,
+                                               uint32_t L, uint32_t Lh, uint32_t colour) {
   const uint32_t p = (colour + y + z) & 1u;  // x = 2*xh + p
   const uint32_t plane = L * Lh;
   const uint32_t row = (z * L + y) * Lh;
@@ -250,12 +275,12 @@ __device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __rest
   const uint32_t q_ym = y == 0 ? q + (L - 1) * Lh : q - Lh;
   const uint32_t q_zp = z + 1 == L ? q - (L - 1) * plane : q + plane;
   const uint32_t q_zm = z == 0 ? q + (L - 1) * plane : q - plane;
-  in.sxp = __ldg(oth + q_xp);
-  in.sxm = __ldg(oth + q_xm);
-  in.syp = __ldg(oth + q_yp);
-  in.sym = __ldg(oth + q_ym);
-  in.szp = __ldg(oth + q_zp);
-  in.szm = __ldg(oth + q_zm);
+  in.sxp = oth.ldg(q_xp);
+  in.sxm = oth.ldg(q_xm);
+  in.syp = oth.ldg(q_yp);
+  in.sym = oth.ldg(q_ym);
+  in.szp = oth.ldg(q_zp);
+  in.szm = oth.ldg(q_zm);
   in.jxp = __ldg(jx_own + q);
   in.jxm = __ldg(jx_oth + q_xm);
   in.jyp = __ldg(jy_own + q);
@@ -264,11 +289,22 @@ __device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __rest
   in.jzm = __ldg(jz_oth + q_zm);
   in.s = make_float3(0.0f, 0.0f, 0.0f);
   if constexpr (U != U_HB) {
-    const float4 o = own[q];
+    const float4 o = own.ld(q);
     in.s = make_float3(o.x, o.y, o.z);
   }
   in.q = q;
   in.site = (2 * xh + p) + y * L + z * L * L;
+}
+
+template <int U>
+__device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __restrict__ own,
+                                            const float4* __restrict__ oth, const float* __restrict__ jx_own,
+                                            const float* __restrict__ jy_own, const float* __restrict__ jz_own,
+                                            const float* __restrict__ jx_oth, const float* __restrict__ jy_oth,
+                                            const float* __restrict__ jz_oth, uint32_t xh, uint32_t y, uint32_t z,
+                                            uint32_t L, uint32_t Lh, uint32_t colour) {
+  gather_site_in<U>(in, SpinsF4{const_cast<float4*>(own)}, SpinsF4{const_cast<float4*>(oth)}, jx_own, jy_own, jz_own,
+                    jx_oth, jy_oth, jz_oth, xh, y, z, L, Lh, colour);
 }
 
 // Form h (Eq. 2) and apply update U: the site's new spin.
@@ -304,6 +340,22 @@ __device__ __forceinline__ void half_sweep_site(float4* __restrict__ own, const 
   SiteInputs in;
   gather_site<U>(in, own, oth, jx_own, jy_own, jz_own, jx_oth, jy_oth, jz_oth, xh, y, z, L, Lh, colour);
   finish_site<U>(in, own, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+}
+
+// One site of a half-sweep in the packed layout (same arithmetic).
+template <int U>
+__device__ __forceinline__ void half_sweep_site_packed(SpinsSoA own, SpinsSoA oth, const float* __restrict__ jx_own,
+                                                       const float* __restrict__ jy_own,
+                                                       const float* __restrict__ jz_own,
+                                                       const float* __restrict__ jx_oth,
+                                                       const float* __restrict__ jy_oth,
+                                                       const float* __restrict__ jz_oth, uint32_t xh, uint32_t y,
+                                                       uint32_t z, uint32_t L, uint32_t Lh, uint32_t colour,
+                                                       uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0, uint32_t k1,
+                                                       float beta, float step, int hits) {
+  SiteInputs in;
+  gather_site_in<U>(in, own, oth, jx_own, jy_own, jz_own, jx_oth, jy_oth, jz_oth, xh, y, z, L, Lh, colour);
+  own.st(in.q, site_result<U>(in, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits));
 }
 
 // Unsigned division by an invariant d (Granlund & Montgomery, "Division by

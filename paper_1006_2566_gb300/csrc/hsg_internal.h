@@ -26,6 +26,10 @@ struct SweepArgs {
   // When set, the sweep counter is read from this device word instead of
   // sweep_lo/sweep_hi (so that a captured graph can be replayed).
   const unsigned long long* sweep_ptr;
+  // Packed layout: own / oth are then component-0 arrays of three fp32
+  // arrays `stride` floats apart (global kernel only).
+  bool packed;
+  size_t stride;
 };
 
 // Kernel variants (values match HSG_KERNEL_*).
@@ -48,8 +52,10 @@ struct WaveArgs {
 // colour-0 and colour-1 half-sweeps of launch_half_sweep(U_OR, ...).
 cudaError_t launch_or_sweep_wave(const WaveArgs& a, int sm_count, cudaStream_t s);
 
-// Spin initialisation: S[2][N/2] from Philox kind INIT.  One launch.
-cudaError_t launch_init_spins(float4* S, int L, uint32_t k0, uint32_t k1, cudaStream_t s);
+// Spin layouts (hsg_device.cuh): `packed` = three fp32 component arrays per
+// colour (12 bytes a spin), else float4 per spin.
+// Spin initialisation: S from Philox kind INIT.  One launch.
+cudaError_t launch_init_spins(void* S, bool packed, int L, uint32_t k0, uint32_t k1, cudaStream_t s);
 
 // Site-major -> colour-split couplings (src: 3N fp32 or fp64).  One launch.
 cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s);
@@ -60,28 +66,28 @@ cudaError_t launch_gen_couplings(float* J, int L, uint32_t k0, uint32_t k1, cuda
 cudaError_t launch_gather_couplings(const float* J, float* dst, int L, cudaStream_t s);
 
 // Site-major fp32 spins <-> colour-split float4 spins.  One launch each.
-cudaError_t launch_scatter_spins(const float* src, float4* S, int L, cudaStream_t s);
-cudaError_t launch_gather_spins(const float4* S, float* dst, int L, cudaStream_t s);
+cudaError_t launch_scatter_spins(const float* src, void* S, bool packed, int L, cudaStream_t s);
+cudaError_t launch_gather_spins(const void* S, bool packed, float* dst, int L, cudaStream_t s);
 
 // Spins (3 per site) and +x/+y/+z bonds of n listed site-major indices
 // (device arrays).  One launch (none for n = 0).
-cudaError_t launch_gather_sites(const float4* S, const float* J, int L, const uint32_t* sites, int n, float* spins,
-                                float* bonds, cudaStream_t s);
+cudaError_t launch_gather_sites(const void* S, bool packed, const float* J, int L, const uint32_t* sites, int n,
+                                float* spins, float* bonds, cudaStream_t s);
 
 // Energy: number of FP64 partial sums the first pass writes, and the
 // two-pass E/N into *out (device).  Two launches.
 // With log_idx set, E/N goes to out[*log_idx] and *log_idx is incremented
 // (an energy log whose position lives in device memory).
 size_t energy_partials(int L);
-cudaError_t launch_energy(const float4* S, const float* J, int L, double* partials, double* out,
+cudaError_t launch_energy(const void* S, bool packed, const float* J, int L, double* partials, double* out,
                           unsigned long long* log_idx, cudaStream_t s);
 
 // Device counters: *p = v, *p += d.  One single-thread launch each.
 cudaError_t launch_set_u64(unsigned long long* p, unsigned long long v, cudaStream_t s);
 cudaError_t launch_add_u64(unsigned long long* p, unsigned long long d, cudaStream_t s);
 
-// FP64 renormalisation of n float4 spins.  One launch.
-cudaError_t launch_renorm(float4* S, long long n, int sm_count, cudaStream_t s);
+// FP64 renormalisation of the n = N spins.  One launch.
+cudaError_t launch_renorm(void* S, bool packed, long long n, int sm_count, cudaStream_t s);
 
 // Record the calling thread's last error message (read by hsg_last_error(NULL)).
 void set_thread_error(const std::string& msg);

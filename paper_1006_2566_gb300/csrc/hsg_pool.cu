@@ -534,7 +534,7 @@ hsg_status hsg_pool_admit(hsg_pool* p, int L, uint64_t seed, uint32_t sample, ui
   float* Jd = reinterpret_cast<float*>(p->arena + off + sizeof(float4) * n);
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu);
   const uint32_t k1 = (uint32_t)(seed >> 32) ^ ((2u * sample + replica) * 0x9E3779B9u);
-  cudaError_t e = hsg::launch_init_spins(S, L, k0, k1, p->stream);
+  cudaError_t e = hsg::launch_init_spins(S, false, L, k0, k1, p->stream);
   p->launches += 1;
   if (e == cudaSuccess) {
     if (!J) {
@@ -669,7 +669,7 @@ hsg_status hsg_pool_get_spins(hsg_pool* p, int slot, float* out, int where) {
     if (st != HSG_OK) return st;
     dst = static_cast<float*>(p->stage);
   }
-  cudaError_t e = hsg::launch_gather_spins(reinterpret_cast<const float4*>(p->arena + s.off), dst, s.L, p->stream);
+  cudaError_t e = hsg::launch_gather_spins(p->arena + s.off, false, dst, s.L, p->stream);
   p->launches += 1;
   if (e == cudaSuccess && where == HSG_HOST) {
     e = cudaMemcpyAsync(out, dst, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, p->stream);

@@ -54,6 +54,31 @@ __global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
                      (uint32_t)a.colour, sweep_lo, sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
 }
 
+// The global variant over the packed layout (three fp32 arrays per colour,
+// 12 bytes a spin: 60 bytes per over-relaxation update instead of 72).  Same
+// site code on the same values, so bit-identical to the float4 kernel.
+template <int U>
+__global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
+    k_half_sweep_global_packed(const SweepArgs a) {
+  const uint32_t xh = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
+  const uint32_t z = blockIdx.z;
+  const uint32_t L = a.L, Lh = a.Lh;
+  if (xh >= Lh || y >= L) return;
+  uint32_t sweep_lo = a.sweep_lo, sweep_hi = a.sweep_hi;
+  if constexpr (U != U_OR) {
+    if (a.sweep_ptr) {
+      const unsigned long long sw = *a.sweep_ptr;
+      sweep_lo = (uint32_t)sw;
+      sweep_hi = (uint32_t)(sw >> 32);
+    }
+  }
+  const SpinsSoA own{reinterpret_cast<float*>(a.own), a.stride};
+  const SpinsSoA oth{const_cast<float*>(reinterpret_cast<const float*>(a.oth)), a.stride};
+  half_sweep_site_packed<U>(own, oth, a.jx_own, a.jy_own, a.jz_own, a.jx_oth, a.jy_oth, a.jz_oth, xh, y, z, L, Lh,
+                            (uint32_t)a.colour, sweep_lo, sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
+}
+
 // ---------------------------------------------------------------------------
 // Slab variant.
 // ---------------------------------------------------------------------------
@@ -128,7 +153,11 @@ __global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
 
 template <int U>
 cudaError_t launch_kind(int variant, const SweepArgs& a, cudaStream_t s) {
-  if (variant == V_SLAB) {
+  if (a.packed) {
+    const dim3 block = a.Lh >= 64 ? dim3(64, 2) : dim3(32, 4);
+    const dim3 grid(cdiv(a.Lh, block.x), cdiv(a.L, block.y), (unsigned)a.L);
+    k_half_sweep_global_packed<U><<<grid, block, 0, s>>>(a);
+  } else if (variant == V_SLAB) {
     const dim3 grid(cdiv(a.Lh, TX), cdiv(a.L, TY), cdiv(a.L, ZC));
     k_half_sweep_slab<U><<<grid, dim3(TX, TY), 0, s>>>(a);
   } else {

@@ -24,6 +24,7 @@ HSG_PROP_SPHERE, HSG_PROP_BALL = 0, 1
 HSG_F32, HSG_F64 = 0, 1
 HSG_HOST, HSG_DEVICE = 0, 1
 HSG_KERNEL_AUTO, HSG_KERNEL_GLOBAL, HSG_KERNEL_SLAB, HSG_KERNEL_WAVE = 0, 1, 2, 3
+HSG_LAYOUT_FLOAT4, HSG_LAYOUT_PACKED = 0, 1
 (HSG_PROF_INIT, HSG_PROF_LAYOUT, HSG_PROF_OVERRELAX, HSG_PROF_METROPOLIS, HSG_PROF_HEATBATH,
  HSG_PROF_ENERGY, HSG_PROF_RENORM, HSG_PROF_COUNT) = range(8)
 
@@ -64,6 +65,7 @@ _sch_p = ctypes.POINTER(hsg_schedule)
 
 _SIGS = {
     "hsg_create": ([ctypes.POINTER(_vp), _i, _u64, _u32, _u32, _vp], _i),
+    "hsg_create_layout": ([ctypes.POINTER(_vp), _i, _u64, _u32, _u32, _vp, _i], _i),
     "hsg_destroy": ([_vp], _i),
     "hsg_set_couplings": ([_vp, _vp, _i, _i], _i),
     "hsg_generate_couplings": ([_vp], _i),
@@ -151,9 +153,20 @@ def _array_ptr(a, want_dtype=None):
 # C names
 # ---------------------------------------------------------------------------
 
-def hsg_create(L: int, seed: int, sample: int = 0, replica: int = 0, stream=None) -> ctypes.c_void_p:
+def hsg_create(L: int, seed: int, sample: int = 0, replica: int = 0, stream=None,
+               layout: int = HSG_LAYOUT_FLOAT4) -> ctypes.c_void_p:
+    if layout != HSG_LAYOUT_FLOAT4:
+        return hsg_create_layout(L, seed, sample, replica, stream, layout)
     ctx = _vp()
     _check(_lib.hsg_create(ctypes.byref(ctx), int(L), int(seed), int(sample), int(replica), _stream_ptr(stream)))
+    return ctx
+
+
+def hsg_create_layout(L: int, seed: int, sample: int = 0, replica: int = 0, stream=None,
+                      layout: int = HSG_LAYOUT_PACKED) -> ctypes.c_void_p:
+    ctx = _vp()
+    _check(_lib.hsg_create_layout(ctypes.byref(ctx), int(L), int(seed), int(sample), int(replica),
+                                  _stream_ptr(stream), int(layout)))
     return ctx
 
 
@@ -316,10 +329,12 @@ def hsg_energy_noalloc(L: int, spins, J, e_out, stream=None) -> None:
 class Lattice:
     """One L^3 lattice on the current CUDA device (a thin wrapper over a context)."""
 
-    def __init__(self, L: int, seed: int, sample: int = 0, replica: int = 0, stream=None):
+    def __init__(self, L: int, seed: int, sample: int = 0, replica: int = 0, stream=None,
+                 layout: int = HSG_LAYOUT_FLOAT4):
         self.L = int(L)
         self.N = self.L ** 3
-        self.ctx = hsg_create(L, seed, sample, replica, stream)
+        self.ctx = None
+        self.ctx = hsg_create(L, seed, sample, replica, stream, layout)
 
     def close(self) -> None:
         if self.ctx is not None and self.ctx.value:
