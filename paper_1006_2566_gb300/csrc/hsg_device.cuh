@@ -259,22 +259,40 @@ struct SiteInputs {
 
 // Gather the inputs of site (x = 2 xh + p, y, z) of colour `colour` (layout
 // at the top of this file).  Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.
+// Indices a site of colour `colour` at (x = 2 xh + p, y, z) reads: its own
+// q, its six other-colour neighbours (periodic wrap by compare-and-select,
+// no power-of-2 assumption) and its Philox site number x + y L + z L^2.
+// Host and device: the CPU tests check it against coordinate arithmetic.
+struct SiteIndex {
+  uint32_t q, q_xp, q_xm, q_yp, q_ym, q_zp, q_zm, site;
+};
+
+__host__ __device__ __forceinline__ SiteIndex site_index(uint32_t xh, uint32_t y, uint32_t z, uint32_t L, uint32_t Lh,
+                                                         uint32_t colour) {
+  const uint32_t p = (colour + y + z) & 1u;  // x = 2*xh + p
+  const uint32_t plane = L * Lh;
+  const uint32_t row = (z * L + y) * Lh;
+  SiteIndex i;
+  i.q = row + xh;
+  i.q_xp = p ? (xh + 1 == Lh ? row : i.q + 1) : i.q;
+  i.q_xm = p ? i.q : (xh == 0 ? row + Lh - 1 : i.q - 1);
+  i.q_yp = y + 1 == L ? i.q - (L - 1) * Lh : i.q + Lh;
+  i.q_ym = y == 0 ? i.q + (L - 1) * Lh : i.q - Lh;
+  i.q_zp = z + 1 == L ? i.q - (L - 1) * plane : i.q + plane;
+  i.q_zm = z == 0 ? i.q + (L - 1) * plane : i.q - plane;
+  i.site = (2 * xh + p) + y * L + z * L * L;
+  return i;
+}
+
 template <int U, class Spins>
 __device__ __forceinline__ void gather_site_in(SiteInputs& in, Spins own, Spins oth, const float* __restrict__ jx_own,
                                                const float* __restrict__ jy_own, const float* __restrict__ jz_own,
                                                const float* __restrict__ jx_oth, const float* __restrict__ jy_oth,
                                                const float* __restrict__ jz_oth, uint32_t xh, uint32_t y, uint32_t z,
                                                uint32_t L, uint32_t Lh, uint32_t colour) {
-  const uint32_t p = (colour + y + z) & 1u;  // x = 2*xh + p
-  const uint32_t plane = L * Lh;
-  const uint32_t row = (z * L + y) * Lh;
-  const uint32_t q = row + xh;
-  const uint32_t q_xp = p ? (xh + 1 == Lh ? row : q + 1) : q;
-  const uint32_t q_xm = p ? q : (xh == 0 ? row + Lh - 1 : q - 1);
-  const uint32_t q_yp = y + 1 == L ? q - (L - 1) * Lh : q + Lh;
-  const uint32_t q_ym = y == 0 ? q + (L - 1) * Lh : q - Lh;
-  const uint32_t q_zp = z + 1 == L ? q - (L - 1) * plane : q + plane;
-  const uint32_t q_zm = z == 0 ? q + (L - 1) * plane : q - plane;
+  const SiteIndex ix = site_index(xh, y, z, L, Lh, colour);
+  const uint32_t q = ix.q, q_xp = ix.q_xp, q_xm = ix.q_xm, q_yp = ix.q_yp, q_ym = ix.q_ym, q_zp = ix.q_zp,
+                 q_zm = ix.q_zm;
   in.sxp = oth.ldg(q_xp);
   in.sxm = oth.ldg(q_xm);
   in.syp = oth.ldg(q_yp);
@@ -293,7 +311,7 @@ __device__ __forceinline__ void gather_site_in(SiteInputs& in, Spins own, Spins 
     in.s = make_float3(o.x, o.y, o.z);
   }
   in.q = q;
-  in.site = (2 * xh + p) + y * L + z * L * L;
+  in.site = ix.site;
 }
 
 template <int U>
@@ -366,8 +384,20 @@ struct FastDiv {
   uint32_t m, s1, s2;
 };
 
-__device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) {
+// The constants for divisor d >= 1 (host).
+inline FastDiv make_fastdiv(uint32_t d) {
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;  // ceil(log2 d)
+  const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
+  return FastDiv{(uint32_t)m, l < 1 ? l : 1u, l > 1 ? l - 1 : 0u};
+}
+
+__host__ __device__ __forceinline__ uint32_t fast_div(uint32_t n, FastDiv f) {
+#ifdef __CUDA_ARCH__
   const uint32_t t = __umulhi(n, f.m);
+#else
+  const uint32_t t = (uint32_t)(((unsigned long long)n * f.m) >> 32);
+#endif
   return (t + ((n - t) >> f.s1)) >> f.s2;
 }
 

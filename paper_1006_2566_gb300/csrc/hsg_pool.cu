@@ -43,12 +43,6 @@ struct PoolDesc {
 };
 static_assert(sizeof(PoolDesc) == 96, "PoolDesc layout");
 
-hsg::FastDiv make_fastdiv(uint32_t d) {
-  uint32_t l = 0;
-  while ((1ull << l) < d) ++l;  // ceil(log2 d)
-  const unsigned long long m = ((1ull << 32) * ((1ull << l) - d)) / d + 1;
-  return hsg::FastDiv{(uint32_t)m, l < 1 ? l : 1u, l > 1 ? l - 1 : 0u};
-}
 
 // Site index q -> (xh, y, z) of a slot.
 __device__ __forceinline__ void decode_site(const PoolDesc* d, uint32_t q, uint32_t& xh, uint32_t& y, uint32_t& z) {
@@ -363,8 +357,8 @@ hsg_status sync_tables(hsg_pool* p) {
     d.active = 1;
     d.spin_off = s.off / sizeof(float4);
     d.j_off = (s.off + sizeof(float4) * n) / sizeof(float);
-    d.by_plane = make_fastdiv(d.plane);
-    d.by_lh = make_fastdiv(d.Lh);
+    d.by_plane = hsg::make_fastdiv(d.plane);
+    d.by_lh = hsg::make_fastdiv(d.Lh);
     d.tile_begin = nt;
     for (uint32_t q0 = 0; q0 < d.nh; q0 += (uint32_t)p->tile_sites) p->h_tiles[nt++] = make_uint2((uint32_t)i, q0);
     d.tile_count = nt - d.tile_begin;

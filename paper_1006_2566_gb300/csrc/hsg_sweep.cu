@@ -19,7 +19,7 @@ namespace {
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
-__device__ __forceinline__ uint32_t site_index(int xh, int p, int y, int z, int L) {
+__device__ __forceinline__ uint32_t site_number(int xh, int p, int y, int z, int L) {
   return (uint32_t)(2 * xh + p) + (uint32_t)y * (uint32_t)L + (uint32_t)z * (uint32_t)L * (uint32_t)L;
 }
 
@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
       }
       const float3 h = local_field(buf[ty + 1][tx + 1 + p], buf[ty + 1][tx + p], buf[ty + 2][tx + 1],
                                    buf[ty][tx + 1], s_zp, s_zm, jxp, jxm, jyp, jym, jzp, jzm);
-      const float3 t = update_site<U>(s, h, site_index(xh, p, y, z, L), (uint32_t)a.colour, sweep_lo, sweep_hi,
+      const float3 t = update_site<U>(s, h, site_number(xh, p, y, z, L), (uint32_t)a.colour, sweep_lo, sweep_hi,
                                       a.k0, a.k1, a.beta, a.step, a.hits);
       a.own[q] = make_float4(t.x, t.y, t.z, 0.0f);
       jzm = jz_here;

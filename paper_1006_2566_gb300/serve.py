@@ -100,16 +100,25 @@ def _updates(req: Request, passes: int) -> int:
 
 
 def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots: int, stream=None,
-          tick_sweeps: int = 10, keep_spins: bool = False, autotune: bool = True) -> tuple[list[Result], ServeStats]:
+          tick_sweeps: int = 10, keep_spins: bool = False, autotune: bool = True,
+          cancels: dict[int, float] | None = None, pool_factory=None) -> tuple[list[Result], ServeStats]:
     """Run the request loop in real time (arrivals are honoured on the wall
     clock from the call).  sched_kw: the schedule of every request
-    (hsg.schedule keywords without T).  Returns per-request results in
-    completion order and summary statistics."""
-    import torch
-
+    (hsg.schedule keywords without T).  cancels: request id -> time (seconds
+    from the start) at which its client withdraws it -- a request still
+    waiting is dropped, an admitted one is retired at the next tick (its
+    memory freed for the next admission); the other lattices are untouched.
+    pool_factory(budget_bytes, max_slots, stream) makes the pool (hsg.Pool by
+    default).  Returns per-request results in completion order and summary
+    statistics (ids of withdrawn requests in stats.extra["cancelled"], of
+    requests larger than the whole pool in stats.extra["rejected"])."""
     from . import hsg
 
     sched = hsg.schedule(**sched_kw)
+    make_pool = pool_factory or hsg.Pool
+    cancel_at = dict(cancels or {})
+    cancelled: list[int] = []
+    rejected: list[int] = []  # larger than the whole pool
     passes = (1 if sched_kw.get("kind", hsg.HSG_NONE) != hsg.HSG_NONE else 0) + sched_kw.get("n_or", 0)
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     waiting: collections.deque[Request] = collections.deque()
@@ -117,12 +126,25 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
     results: list[Result] = []
     ticks = max_batch = 0
     tuned = not autotune
-    with hsg.Pool(budget_bytes, max_slots, stream) as pool:
+    with make_pool(budget_bytes, max_slots, stream) as pool:
         t0 = time.perf_counter()
         while pending or waiting or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
+            if cancel_at:  # withdrawals that are due
+                due = {rid for rid, tc in cancel_at.items() if tc <= now}
+                for rid in due:
+                    del cancel_at[rid]
+                    for q in (pending, waiting):
+                        hit = [r for r in q if r.rid == rid]
+                        for r in hit:
+                            q.remove(r)
+                            cancelled.append(rid)
+                    for slot in [sl for sl, a in active.items() if a[0].rid == rid]:
+                        pool.retire(slot)
+                        del active[slot]
+                        cancelled.append(rid)
             while waiting:  # admit in arrival order while a slot and memory are free
                 r = waiting[0]
                 try:
@@ -134,7 +156,9 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
                 waiting.popleft()
                 active[slot] = [r, r.sweeps, time.perf_counter() - t0]
             if not active:
-                if pending:
+                if waiting:  # an empty pool refused it: it can never be admitted
+                    rejected.append(waiting.popleft().rid)
+                elif pending:
                     time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
                 continue
             if not tuned and len(active) >= 8:
@@ -160,12 +184,15 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
             elif stream is not None:
                 stream.synchronize()
             else:
+                import torch
+
                 torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     p50, p99, mean = latency_stats(results)
     by_id = {q.rid: q for q in requests}
     upd = sum(_updates(by_id[r.rid], passes) for r in results)
-    return results, ServeStats(len(results), wall, upd, p50, p99, mean, max_batch, ticks)
+    return results, ServeStats(len(results), wall, upd, p50, p99, mean, max_batch, ticks,
+                               extra={"cancelled": cancelled, "rejected": rejected})
 
 
 def serve_fifo(requests: list[Request], sched_kw: dict, stream=None, keep_spins: bool = False):

@@ -45,3 +45,23 @@ def test_each_result_is_the_same_alone_and_in_the_mix(hsg):
     for f in fifo:
         assert np.array_equal(f.spins, by_id[f.rid].spins)
         assert abs(f.energy - by_id[f.rid].energy) <= 2e-6
+
+
+def test_withdrawn_requests_leave_the_others_unchanged(hsg):
+    """Clients withdraw two requests (one while it runs, one before it is
+    admitted); every other result is still bit-identical to its request run
+    alone, and the withdrawn lattice's memory goes to the next admission."""
+    reqs = serve.poisson_trace(10, rate_per_s=200.0, seed=9, sides=(8, 16, 24), sweep_range=(10, 40))
+    kw = dict(kind=hsg.HSG_HEATBATH, n_or=1, renorm_every=5)
+    budget = 2 * 28 * 24 ** 3
+    first, last = reqs[0].rid, reqs[-1].rid
+    res, st = serve.serve(reqs, kw, budget, 4, torch.cuda.Stream(), tick_sweeps=2, keep_spins=True,
+                          autotune=False, cancels={first: reqs[0].arrival + 1e-4, last: 0.0})
+    assert sorted(st.extra["cancelled"]) == sorted([first, last])
+    assert st.completed == len(reqs) - 2
+    for r in res:
+        q = next(x for x in reqs if x.rid == r.rid)
+        with hsg.Lattice(q.L, q.seed, q.sample, 0) as lat:
+            lat.generate_couplings()
+            lat.sweep(hsg.schedule(T=q.T, **kw), q.sweeps)
+            assert np.array_equal(r.spins, lat.spins()), q

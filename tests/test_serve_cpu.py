@@ -34,3 +34,113 @@ def test_latency_statistics():
     assert p99 == pytest.approx(99.01)
     assert mean == pytest.approx(50.5)
     assert all(np.isnan(v) for v in serve.latency_stats([]))
+
+
+class FakePool:
+    """A pool with the hsg.Pool interface and no GPU: each admitted lattice
+    takes L^3 bytes of the budget; every sweep adds k to its counter;
+    energies are -(sweeps done)/1000 per slot, so results show how far each
+    lattice ran.  Records admissions and retirements."""
+
+    def __init__(self, budget, max_slots, stream=None):
+        self.budget, self.max_slots = budget, max_slots
+        self.slots = {}  # slot -> [L, sweeps]
+        self.log = []
+        FakePool.last = self
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.closed = True
+
+    def admit(self, L, seed, sample, replica, T):
+        from paper_1006_2566_gb300 import hsg
+
+        used = sum(v[0] ** 3 for v in self.slots.values())
+        if used + L ** 3 > self.budget or len(self.slots) >= self.max_slots:
+            raise hsg.HsgError(hsg.HSG_EBUSY, "busy")
+        slot = min(set(range(self.max_slots)) - set(self.slots))
+        self.slots[slot] = [L, 0]
+        self.log.append(("admit", sample, slot))
+        return slot
+
+    def retire(self, slot):
+        self.log.append(("retire", slot))
+        del self.slots[slot]
+
+    def sweep(self, sched, k):
+        for v in self.slots.values():
+            v[1] += k
+
+    def energies(self):
+        return np.array([-self.slots[s][1] / 1000.0 if s in self.slots else np.nan for s in range(self.max_slots)])
+
+    def spins(self, slot):
+        return np.zeros(3 * self.slots[slot][0] ** 3, dtype=np.float32)
+
+
+class SyncStream:
+    def synchronize(self):
+        pass
+
+
+def reqs(spec):
+    return [serve.Request(k, t, L, 1, k, 0.5, sw) for k, (t, L, sw) in enumerate(spec)]
+
+
+def test_serve_loop_admits_in_order_under_the_budget_and_runs_each_to_its_sweeps():
+    pytest.importorskip("torch")
+    rq = reqs([(0.0, 8, 30), (0.0, 8, 20), (0.0, 8, 40), (0.0, 6, 10)])
+    res, st = serve.serve(rq, dict(kind=1, n_or=1), budget_bytes=2 * 8 ** 3, max_slots=4, stream=SyncStream(),
+                          autotune=False, pool_factory=FakePool)
+    by = {r.rid: r for r in res}
+    assert sorted(by) == [0, 1, 2, 3] and st.completed == 4
+    for r in rq:
+        assert by[r.rid].energy == -r.sweeps / 1000.0  # each ran exactly its sweeps
+    admits = [e[1] for e in FakePool.last.log if e[0] == "admit"]
+    assert admits == [0, 1, 2, 3]  # arrival order; request 2 waited for memory
+    assert st.max_batch == 2 and st.extra == {"cancelled": [], "rejected": []}
+
+
+class SlowPool(FakePool):
+    """2 ms per pool sweep call, so that wall-clock withdrawals land mid-run."""
+
+    def sweep(self, sched, k):
+        import time
+
+        time.sleep(0.002)
+        super().sweep(sched, k)
+
+
+def test_serve_loop_withdraws_waiting_and_running_requests():
+    pytest.importorskip("torch")
+    # request 0 needs 40 ticks (>= 80 ms) and is withdrawn at 50 ms; 1 and 2
+    # finish within ~20 ms; 3 is withdrawn before it arrives; 99 is unknown
+    rq = reqs([(0.0, 8, 400), (0.0, 8, 50), (0.0, 8, 30), (0.2, 6, 10)])
+    res, st = serve.serve(rq, dict(kind=1, n_or=1), budget_bytes=2 * 8 ** 3, max_slots=4, stream=SyncStream(),
+                          tick_sweeps=10, autotune=False, pool_factory=SlowPool,
+                          cancels={0: 0.05, 3: 0.0, 99: 0.0})
+    by = {r.rid: r for r in res}
+    assert sorted(by) == [1, 2]  # 0 withdrawn while running, 3 before it arrived
+    assert by[1].energy == -0.05 and by[2].energy == -0.03
+    assert sorted(st.extra["cancelled"]) == [0, 3]
+    retired = [e[1] for e in FakePool.last.log if e[0] == "retire"]
+    assert len(retired) == 3  # the withdrawn lattice freed its slot too
+
+
+def test_serve_loop_rejects_a_request_larger_than_the_pool_and_propagates_errors():
+    pytest.importorskip("torch")
+    rq = reqs([(0.0, 8, 10), (0.0, 16, 10)])
+    res, st = serve.serve(rq, dict(kind=1), budget_bytes=8 ** 3, max_slots=2, stream=SyncStream(),
+                          autotune=False, pool_factory=FakePool)
+    assert [r.rid for r in res] == [0] and st.extra["rejected"] == [1]
+
+    class Failing(FakePool):
+        def sweep(self, sched, k):
+            raise RuntimeError("injected device error")
+
+    with pytest.raises(RuntimeError, match="injected"):
+        serve.serve(reqs([(0.0, 8, 10)]), dict(kind=1), budget_bytes=8 ** 3, max_slots=1, stream=SyncStream(),
+                    autotune=False, pool_factory=Failing)
+    assert FakePool.last.closed  # the pool is released on the way out
