@@ -28,9 +28,8 @@
 // launch_half_sweep exactly.
 //
 // Shape (measured on GB300 at L = 256): 16 x 14 tiles make R0 exactly nine
-// warps; three CTAs per SM; shared memory kept to 51 KB per CTA, because the
-// rest of the SM's L1 serves the overlapping bond lines of stage 0 (the same
-// kernel with all of L1 given to shared memory ran 1.6 x slower).  The
+// warps; 51 KB of shared memory per CTA, three CTAs per SM, and the rest of
+// the SM's unified L1/shared array left to L1 (launch_wave).  The
 // heat-bath is not blocked this way: recomputing the halo's Philox draws and
 // transcendentals made it compute-bound and slower than two half-sweeps.
 #include "hsg_device.cuh"
@@ -45,7 +44,7 @@ constexpr int R1N = R1X * R1Y;             // 360
 constexpr int R0X = WX + 2, R0Y = WY + 2;  // colour-0 region: halo 1
 constexpr int R0N = R0X * R0Y;             // 288
 constexpr int W_THREADS = R0N;             // nine warps
-constexpr int W_MIN_BLOCKS = 3;            // resident CTAs per SM aimed at
+constexpr int W_MIN_BLOCKS = 3;            // resident CTAs per SM (at most 72 registers)
 constexpr int NS1 = 4, NS0 = 3;            // ring slots
 constexpr int MIN_ZC = 8;                  // shortest z chunk
 static_assert(W_THREADS % 32 == 0 && WX * WY <= W_THREADS && R1N <= 2 * W_THREADS, "thread roles");
@@ -284,18 +283,31 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
   }
 }
 
+// Launch shape, measured at L = 256 (OR sweep time; bit-identical results
+// in every case):
+//  * carveout hint 58 %: the driver takes the next supported configuration,
+//    164 KB of shared memory -- the smallest that holds three 51 KB CTAs --
+//    and leaves 92 KB of the SM's unified array as L1 for the in-flight bond
+//    loads of stage 0: 166 us.  With 60 KB of L1 left (196 KB shared) 178 us,
+//    with 28 KB 267 us;
+//  * grid: three CTAs per SM over the tiles (z chunks of L / 3 at L = 256),
+//    one full wave: 166 us; six per SM (two waves) 167 us; two per SM 196 us;
+//    four per SM (a partial second wave) 234 us.
+constexpr int W_CARVEOUT_PCT = 58;
+constexpr int W_GRID_PER_SM = 3;
+
 cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
-  static int per_sm = 0;  // resident CTAs per SM
-  if (per_sm == 0) {
+  static bool configured = false;
+  if (!configured) {
     cudaError_t e =
         cudaFuncSetAttribute(k_or_sweep_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_or_sweep_wave, W_THREADS, W_SMEM);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_or_sweep_wave, cudaFuncAttributePreferredSharedMemoryCarveout, W_CARVEOUT_PCT);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
+    configured = true;
   }
   const unsigned tx = cdiv(a.Lh, WX), ty = cdiv(a.L, WY);
-  // As many z chunks as keep every tile column resident in one wave.
-  long long chunks = (long long)per_sm * sm_count / ((long long)tx * ty);
+  long long chunks = (long long)W_GRID_PER_SM * sm_count / ((long long)tx * ty);
   if (chunks < 1) chunks = 1;
   int zc = (int)cdiv(a.L, chunks);
   if (zc < MIN_ZC) zc = MIN_ZC;
