@@ -197,15 +197,50 @@ def profiled_traffic(kernel_variant: str, L: int):
     if it was taken on the current kernel source; else None."""
     name = {"wave": f"or_full_sweep_wave_L{L}.md", "packed": f"or_half_sweep_packed_L{L}.md"}.get(
         kernel_variant, f"or_half_sweep_{kernel_variant}_L{L}.md")
+    return profiled_value(name, "dram_bytes_per_launch")
+
+
+def profiled_value(name: str, key: str):
+    """A per-launch figure `key` from the committed ncu summary `name`, if it
+    was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_src = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]{16})", text)
-    m_tr = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m_src or not m_tr or m_src.group(1) != kernel_source_hash():
+    m_v = re.search(key + r":\s*([0-9.eE+]+)", text)
+    if not m_src or not m_v or m_src.group(1) != kernel_source_hash():
         return None
-    return float(m_tr.group(1))
+    return float(m_v.group(1))
+
+
+# Warp instructions one SM issues per clock: four schedulers, one each.
+ISSUE_PER_SM_CLK = 4
+# Maximum SM clock of a GB300 (MHz), used when no clock was sampled.
+SM_MAX_MHZ_NOMINAL = 2070
+
+
+def alu_roofline(L, hits_per_launch, met_ms, met_n, clk, sm_count, steps, profiled_ms):
+    """The multi-hit Metropolis half-sweep is bound by instruction issue, not
+    by memory: `achieved` = warp instructions it issues per second (the ncu
+    count per launch over the live CUDA-event duration), `peak` = the SMs'
+    issue slots per second at the maximum SM clock."""
+    avg_s = met_ms / met_n / 1e3
+    max_mhz = (clk or {}).get("sm_max_mhz") or SM_MAX_MHZ_NOMINAL
+    peak = sm_count * ISSUE_PER_SM_CLK * max_mhz * 1e6 / 1e9
+    name = f"metropolis_half_sweep_global_L{L}.md"
+    insts = profiled_value(name, "warp_inst_per_launch")
+    ach = insts / avg_s / 1e9 if insts else None
+    return {"bound": "alu", "kernel": "multi-hit Metropolis half-sweep", "unit": "G warp-inst/s",
+            "achieved": round(ach, 1) if ach else None, "peak": round(peak, 1),
+            "frac": round(ach / peak, 4) if ach else None,
+            "peak_source": f"{sm_count} SMs x {ISSUE_PER_SM_CLK} warp instructions/clock x {max_mhz:.0f} MHz",
+            "warp_inst_per_launch": insts, "hits_per_launch": hits_per_launch,
+            "hits_per_ns": round(hits_per_launch / avg_s / 1e9, 2),
+            "traffic": profiled_value(name, "dram_bytes_per_launch"),
+            "avg_launch_ms": round(met_ms / met_n, 5), "launches": met_n,
+            "measured_over": f"{steps} steps with per-launch CUDA events ({profiled_ms / steps:.3f} "
+                             f"ms/step, directly launched)"}
 
 
 def step_units(wl) -> int:
@@ -406,6 +441,10 @@ def run_ours(args, wl):
                                            if wave or packed else None),
                 "measured_over": f"{args.steps} steps with per-launch CUDA events ({profiled_ms / args.steps:.3f} "
                                  f"ms/step, directly launched)"}
+    if met_n and met_ms > or_ms + hb_ms:
+        # Metropolis dominates the step: its roofline is instruction issue.
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        roof = alu_roofline(L, nh * wl["hits"], met_ms, met_n, clk, sm_count, args.steps, profiled_ms)
     kernels = {}
     for name, (ms, n), bpu, u in (("heatbath", (hb_ms, hb_n), b_hb, nh), ("overrelax", (or_ms, or_n), b_or, units),
                                   ("metropolis", (met_ms, met_n), BYTES_OR_PACKED if packed else BYTES_OR, nh)):
