@@ -45,8 +45,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
 }
 
 // (2m+1) * 2^-24 with m the top 23 bits: exact in fp32, strictly inside (0,1).
+// Formed as (1 + m 2^-23) - (1 - 2^-24): m placed in the mantissa of 1.0,
+// minus a constant; the difference is representable, so the subtraction is
+// exact and the value is the same as converting 2m+1 and scaling it.
 __device__ __forceinline__ float u01(uint32_t r) {
-  return __uint2float_rn(((r >> 9) << 1) | 1u) * 5.9604644775390625e-8f;
+  return __int_as_float((int)((r >> 9) | 0x3F800000u)) - 0x1.fffffep-1f;
 }
 
 // Uniform point on S^2 (z = 2 u0 - 1 uniform by Archimedes' theorem).

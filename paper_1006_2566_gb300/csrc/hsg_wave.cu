@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
   for (int s = 0; s < nsteps; ++s) {
     // Ring slots of planes s .. s + 3 (colour 1) and s - 1 .. s + 1 (colour 0).
     const int k0 = s % NS1, k1 = (s + 1) % NS1, k2 = (s + 2) % NS1, k3 = (s + 3) % NS1;
-    const int c0m = (s + 2) % NS0, c00 = s % NS0, c0p = (s + 1) % NS0;
+    const int c00 = s % NS0, c0p = (s + 1) % NS0;
     const uint32_t z1p = z_of(zs, 1), z2p = z_of(zs, 2), z3p = z_of(zs, 3);
     asm volatile("cp.async.wait_all;\n" ::: "memory");  // colour-1 planes up to s + 2
     __syncthreads();  // ... visible to all; step s-1 is done with the slot refilled next
