@@ -331,7 +331,9 @@ hsg_status hsg_pool_destroy(hsg_pool* pool); /* NULL ok; waits for the stream */
 hsg_status hsg_pool_admit(hsg_pool* pool, int L, uint64_t seed, uint32_t sample, uint32_t replica, double T,
                           const void* J, int dtype, int where, int* slot);
 
-/* Release a lattice's slot and arena block (waits for queued work). */
+/* Release a lattice's slot and arena block.  Does not wait: work already
+ * queued for the slot runs first, and the block is reused only by work
+ * queued on the pool's stream after this call (stream order). */
 hsg_status hsg_pool_retire(hsg_pool* pool, int slot);
 
 /* n_sweeps sweeps of every admitted lattice, each at its own temperature
@@ -340,8 +342,19 @@ hsg_status hsg_pool_retire(hsg_pool* pool, int slot);
 hsg_status hsg_pool_sweep(hsg_pool* pool, const hsg_schedule* schedule, int n_sweeps);
 
 /* E/N of every slot into out[0..n) (NaN for free slots); FP32 site terms,
- * FP64 sums, fixed order.  Synchronises. */
+ * FP64 sums, fixed order (Eq. 1, as hsg_energy).  Synchronises. */
 hsg_status hsg_pool_energies(hsg_pool* pool, double* out, int n);
+
+/* The same energies without waiting: hsg_pool_energies_async queues the
+ * energy kernels and the copy of every slot's E/N into the pool's pinned
+ * buffer `buffer` (0 or 1) after the work already queued, and returns;
+ * hsg_pool_energies_read waits for that copy and writes the values into
+ * out[0..n) (NaN for slots free at queueing time and for i >= max_slots).
+ * A slot retired after hsg_pool_energies_async still gets its final E/N.
+ * Reading a buffer with nothing queued is HSG_EINVAL; queueing into a
+ * buffer that was not read waits for and drops its previous values. */
+hsg_status hsg_pool_energies_async(hsg_pool* pool, int buffer);
+hsg_status hsg_pool_energies_read(hsg_pool* pool, int buffer, double* out, int n);
 
 /* One lattice's spins, site-major fp32 (as hsg_get_spins), and counter. */
 hsg_status hsg_pool_get_spins(hsg_pool* pool, int slot, float* out, int where);

@@ -222,16 +222,28 @@ struct hsg_pool {
   std::map<uint64_t, uint64_t> free_blocks;  // offset -> size
   int max_slots = 0, n_active = 0;
   std::vector<Slot> slots;
+  // Device tables and two pinned host mirrors of each: a rebuild writes
+  // the mirror whose last upload has completed (its event), so the host
+  // never waits for the sweeps in flight.
   PoolDesc* d_desc = nullptr;
-  PoolDesc* h_desc = nullptr;  // pinned mirror
+  PoolDesc* h_desc = nullptr;  // pinned, 2 x max_slots
   uint2* d_tiles = nullptr;
-  uint2* h_tiles = nullptr;  // pinned
+  uint2* h_tiles = nullptr;  // pinned, 2 x tiles_cap
   size_t tiles_cap = 0;
   uint32_t* d_ntiles = nullptr;
-  uint32_t* h_ntiles = nullptr;  // pinned
+  uint32_t* h_ntiles = nullptr;  // pinned, 2
+  cudaEvent_t up_ev[2] = {nullptr, nullptr};
+  bool up_rec[2] = {false, false};
+  int up_buf = 0;
   double* d_partials = nullptr;
   double* d_energy = nullptr;
-  double* h_energy = nullptr;  // pinned
+  // Energies read back into pinned buffer b (b = 0, 1 for
+  // hsg_pool_energies_async, 2 for hsg_pool_energies), each followed by
+  // an event that its reader waits for.
+  static constexpr int kEnergyBufs = 3;
+  double* h_energy = nullptr;  // pinned, kEnergyBufs x max_slots
+  cudaEvent_t en_ev[kEnergyBufs] = {nullptr, nullptr, nullptr};
+  bool en_pending[kEnergyBufs] = {false, false, false};
   void* stage = nullptr;
   size_t stage_bytes = 0;
   bool dirty = true;
@@ -315,9 +327,10 @@ hsg_status ensure_pool_stage(hsg_pool* p, size_t bytes) {
 // Host: rebuild the slot table and the work list; device: upload both.
 hsg_status sync_tables(hsg_pool* p) {
   if (!p->dirty) return HSG_OK;
-  // the pinned mirrors may still be the source of an earlier upload
-  cudaError_t e = cudaStreamSynchronize(p->stream);
-  if (e != cudaSuccess) return pcuda(p, e, "pool sync");
+  const int b = p->up_buf;
+  cudaError_t e = cudaSuccess;
+  // this mirror may still be the source of the upload before last
+  if (p->up_rec[b] && (e = cudaEventSynchronize(p->up_ev[b])) != cudaSuccess) return pcuda(p, e, "pool sync");
   size_t need = 0;
   for (const Slot& s : p->slots)
     if (s.active) need += cdiv_u((unsigned long long)s.L * s.L * s.L / 2, (unsigned long long)p->tile_sites);
@@ -325,6 +338,7 @@ hsg_status sync_tables(hsg_pool* p) {
     size_t cap = std::max<size_t>(1024, p->tiles_cap);
     while (cap < need) cap *= 2;
     drop_graph(p);  // the graph holds the old buffer addresses
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return pcuda(p, e, "pool sync");
     if (p->d_tiles) cudaFree(p->d_tiles);
     if (p->h_tiles) cudaFreeHost(p->h_tiles);
     if (p->d_partials) cudaFree(p->d_partials);
@@ -333,15 +347,18 @@ hsg_status sync_tables(hsg_pool* p) {
     p->d_partials = nullptr;
     p->tiles_cap = 0;
     if ((e = cudaMalloc(&p->d_tiles, cap * sizeof(uint2))) != cudaSuccess ||
-        (e = cudaMallocHost(&p->h_tiles, cap * sizeof(uint2))) != cudaSuccess ||
+        (e = cudaMallocHost(&p->h_tiles, 2 * cap * sizeof(uint2))) != cudaSuccess ||
         (e = cudaMalloc(&p->d_partials, cap * sizeof(double))) != cudaSuccess)
       return pcuda(p, e, "pool work list");
     p->tiles_cap = cap;
   }
+  PoolDesc* h_desc = p->h_desc + (size_t)b * p->max_slots;
+  uint2* h_tiles = p->h_tiles + (size_t)b * p->tiles_cap;
+  uint32_t* h_ntiles = p->h_ntiles + b;
   uint32_t nt = 0;
   for (int i = 0; i < p->max_slots; ++i) {
     const Slot& s = p->slots[i];
-    PoolDesc& d = p->h_desc[i];
+    PoolDesc& d = h_desc[i];
     memset(&d, 0, sizeof(d));
     if (!s.active) continue;
     const uint64_t n = (uint64_t)s.L * s.L * s.L;
@@ -360,17 +377,20 @@ hsg_status sync_tables(hsg_pool* p) {
     d.by_plane = hsg::make_fastdiv(d.plane);
     d.by_lh = hsg::make_fastdiv(d.Lh);
     d.tile_begin = nt;
-    for (uint32_t q0 = 0; q0 < d.nh; q0 += (uint32_t)p->tile_sites) p->h_tiles[nt++] = make_uint2((uint32_t)i, q0);
+    for (uint32_t q0 = 0; q0 < d.nh; q0 += (uint32_t)p->tile_sites) h_tiles[nt++] = make_uint2((uint32_t)i, q0);
     d.tile_count = nt - d.tile_begin;
   }
-  *p->h_ntiles = nt;
-  if ((e = cudaMemcpyAsync(p->d_desc, p->h_desc, sizeof(PoolDesc) * p->max_slots, cudaMemcpyHostToDevice,
+  *h_ntiles = nt;
+  if ((e = cudaMemcpyAsync(p->d_desc, h_desc, sizeof(PoolDesc) * p->max_slots, cudaMemcpyHostToDevice,
                            p->stream)) != cudaSuccess ||
-      (nt && (e = cudaMemcpyAsync(p->d_tiles, p->h_tiles, sizeof(uint2) * nt, cudaMemcpyHostToDevice, p->stream)) !=
+      (nt && (e = cudaMemcpyAsync(p->d_tiles, h_tiles, sizeof(uint2) * nt, cudaMemcpyHostToDevice, p->stream)) !=
                  cudaSuccess) ||
-      (e = cudaMemcpyAsync(p->d_ntiles, p->h_ntiles, sizeof(uint32_t), cudaMemcpyHostToDevice, p->stream)) !=
-          cudaSuccess)
+      (e = cudaMemcpyAsync(p->d_ntiles, h_ntiles, sizeof(uint32_t), cudaMemcpyHostToDevice, p->stream)) !=
+          cudaSuccess ||
+      (e = cudaEventRecord(p->up_ev[b], p->stream)) != cudaSuccess)
     return pcuda(p, e, "pool table upload");
+  p->up_rec[b] = true;
+  p->up_buf = 1 - b;
   p->dirty = false;
   return HSG_OK;
 }
@@ -458,18 +478,21 @@ hsg_status hsg_pool_create(hsg_pool** out, uint64_t budget_bytes, int max_slots,
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
   if (e == cudaSuccess) e = cudaMalloc(&p->arena, p->budget);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_desc, sizeof(PoolDesc) * max_slots);
-  if (e == cudaSuccess) e = cudaMallocHost(&p->h_desc, sizeof(PoolDesc) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_desc, 2 * sizeof(PoolDesc) * max_slots);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_ntiles, sizeof(uint32_t));
-  if (e == cudaSuccess) e = cudaMallocHost(&p->h_ntiles, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_ntiles, 2 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_energy, sizeof(double) * max_slots);
-  if (e == cudaSuccess) e = cudaMallocHost(&p->h_energy, sizeof(double) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_energy, hsg_pool::kEnergyBufs * sizeof(double) * max_slots);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->up_ev[i], cudaEventDisableTiming);
+  for (int i = 0; i < hsg_pool::kEnergyBufs && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&p->en_ev[i], cudaEventDisableTiming);
   if (e != cudaSuccess) {
     hsg_status st = pcuda(nullptr, e, "pool creation");
     hsg_pool_destroy(p);
     return st;
   }
   p->free_blocks[0] = p->budget;
-  *p->h_ntiles = 0;
+  p->h_ntiles[0] = p->h_ntiles[1] = 0;
   *out = p;
   return HSG_OK;
 }
@@ -490,6 +513,10 @@ hsg_status hsg_pool_destroy(hsg_pool* p) {
   cudaFree(p->d_partials);
   cudaFree(p->d_energy);
   cudaFreeHost(p->h_energy);
+  for (cudaEvent_t ev : p->up_ev)
+    if (ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : p->en_ev)
+    if (ev) cudaEventDestroy(ev);
   delete p;
   return HSG_OK;
 }
@@ -566,9 +593,8 @@ hsg_status hsg_pool_admit(hsg_pool* p, int L, uint64_t seed, uint32_t sample, ui
 hsg_status hsg_pool_retire(hsg_pool* p, int slot) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
   if (!valid_slot(p, slot)) return pfail(p, HSG_EINVAL, "no such active slot");
-  // kernels queued for this slot must finish before its memory is reused
-  cudaError_t e = cudaStreamSynchronize(p->stream);
-  if (e != cudaSuccess) return pcuda(p, e, "pool sync");
+  // No wait: the kernels already queued for this slot run first, and its
+  // block is reused only by work queued on the same stream after this call.
   Slot& s = p->slots[slot];
   arena_free(p, s.off, s.bytes);
   s.active = false;
@@ -622,12 +648,16 @@ hsg_status hsg_pool_sweep(hsg_pool* p, const hsg_schedule* sched, int n_sweeps) 
   return HSG_OK;
 }
 
-hsg_status hsg_pool_energies(hsg_pool* p, double* out, int n) {
-  if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
-  if (!out || n < 0) return pfail(p, HSG_EINVAL, "bad output buffer");
+namespace {
+
+// Queue the energy kernels of every slot and the copy of the result into
+// pinned buffer b, followed by b's event.
+hsg_status enqueue_energies(hsg_pool* p, int b) {
   hsg_status st = sync_tables(p);
   if (st != HSG_OK) return st;
   cudaError_t e = cudaSuccess;
+  if (p->en_pending[b] && (e = cudaEventSynchronize(p->en_ev[b])) != cudaSuccess) return pcuda(p, e, "pool sync");
+  p->en_pending[b] = false;
   if (p->n_active > 0) {
     k_pool_energy_partial<<<pool_grid(p), 256, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles,
                                                                 reinterpret_cast<const float4*>(p->arena),
@@ -641,13 +671,46 @@ hsg_status hsg_pool_energies(hsg_pool* p, double* out, int n) {
     e = cudaGetLastError();
   }
   p->launches += 2;
-  const int k = std::min(n, p->max_slots);
-  if (e == cudaSuccess && k > 0)
-    e = cudaMemcpyAsync(p->h_energy, p->d_energy, sizeof(double) * k, cudaMemcpyDeviceToHost, p->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p->h_energy + (size_t)b * p->max_slots, p->d_energy, sizeof(double) * p->max_slots,
+                        cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(p->en_ev[b], p->stream);
   if (e != cudaSuccess) return pcuda(p, e, "pool energies");
-  for (int i = 0; i < n; ++i) out[i] = i < k ? p->h_energy[i] : std::nan("");
+  p->en_pending[b] = true;
   return HSG_OK;
+}
+
+// Wait for buffer b's copy and hand out its first n values.
+hsg_status read_energies(hsg_pool* p, int b, double* out, int n) {
+  if (!p->en_pending[b]) return pfail(p, HSG_EINVAL, "no energies queued in this buffer");
+  const cudaError_t e = cudaEventSynchronize(p->en_ev[b]);
+  if (e != cudaSuccess) return pcuda(p, e, "pool energies");
+  p->en_pending[b] = false;
+  const double* h = p->h_energy + (size_t)b * p->max_slots;
+  for (int i = 0; i < n; ++i) out[i] = i < p->max_slots ? h[i] : std::nan("");
+  return HSG_OK;
+}
+
+}  // namespace
+
+hsg_status hsg_pool_energies(hsg_pool* p, double* out, int n) {
+  if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  if (!out || n < 0) return pfail(p, HSG_EINVAL, "bad output buffer");
+  const hsg_status st = enqueue_energies(p, 2);
+  return st != HSG_OK ? st : read_energies(p, 2, out, n);
+}
+
+hsg_status hsg_pool_energies_async(hsg_pool* p, int buffer) {
+  if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
+  return enqueue_energies(p, buffer);
+}
+
+hsg_status hsg_pool_energies_read(hsg_pool* p, int buffer, double* out, int n) {
+  if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
+  if (!out || n < 0) return pfail(p, HSG_EINVAL, "bad output buffer");
+  return read_energies(p, buffer, out, n);
 }
 
 hsg_status hsg_pool_get_spins(hsg_pool* p, int slot, float* out, int where) {

@@ -98,6 +98,8 @@ _SIGS = {
     "hsg_pool_retire": ([_vp, _i], _i),
     "hsg_pool_sweep": ([_vp, _sch_p, _i], _i),
     "hsg_pool_energies": ([_vp, ctypes.POINTER(_d), _i], _i),
+    "hsg_pool_energies_async": ([_vp, _i], _i),
+    "hsg_pool_energies_read": ([_vp, _i, ctypes.POINTER(_d), _i], _i),
     "hsg_pool_get_spins": ([_vp, _i, _vp, _i], _i),
     "hsg_pool_get_sweep": ([_vp, _i, ctypes.POINTER(_u64)], _i),
     "hsg_pool_usage": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_i)], _i),
@@ -444,6 +446,16 @@ def hsg_pool_energies(pool, n: int) -> np.ndarray:
     return out
 
 
+def hsg_pool_energies_async(pool, buffer: int) -> None:
+    _pcheck(_lib.hsg_pool_energies_async(pool, int(buffer)), pool)
+
+
+def hsg_pool_energies_read(pool, buffer: int, n: int) -> np.ndarray:
+    out = np.zeros(int(n), dtype=np.float64)
+    _pcheck(_lib.hsg_pool_energies_read(pool, int(buffer), out.ctypes.data_as(ctypes.POINTER(_d)), int(n)), pool)
+    return out
+
+
 def hsg_pool_get_spins(pool, slot: int, out) -> None:
     ptr, where, code, _ = _array_ptr(out)
     if code != HSG_F32:
@@ -523,6 +535,14 @@ class Pool:
 
     def energies(self) -> np.ndarray:
         return hsg_pool_energies(self.pool, self.max_slots)
+
+    def energies_async(self, buffer: int) -> None:
+        """Queue every slot's E/N into pinned buffer 0 or 1 (no wait)."""
+        hsg_pool_energies_async(self.pool, buffer)
+
+    def energies_read(self, buffer: int) -> np.ndarray:
+        """Wait for the values queued into `buffer` and return them."""
+        return hsg_pool_energies_read(self.pool, buffer, self.max_slots)
 
     def spins(self, slot: int) -> np.ndarray:
         out = np.zeros(3 * self.sides[slot] ** 3, dtype=np.float32)

@@ -99,6 +99,15 @@ def _updates(req: Request, passes: int) -> int:
     return req.L ** 3 * req.sweeps * passes
 
 
+def _marker(stream):
+    """An event recorded on `stream` after the work queued so far."""
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().record_event()
+    return stream.record_event()
+
+
 def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots: int, stream=None,
           tick_sweeps: int = 10, keep_spins: bool = False, autotune: bool = True,
           cancels: dict[int, float] | None = None, pool_factory=None) -> tuple[list[Result], ServeStats]:
@@ -111,7 +120,15 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
     pool_factory(budget_bytes, max_slots, stream) makes the pool (hsg.Pool by
     default).  Returns per-request results in completion order and summary
     statistics (ids of withdrawn requests in stats.extra["cancelled"], of
-    requests larger than the whole pool in stats.extra["rejected"])."""
+    requests larger than the whole pool in stats.extra["rejected"]).
+
+    The host knows when every lattice finishes (its sweep count), so it
+    schedules tick n+1 -- retirements, admissions into the freed memory,
+    the next sweeps -- as soon as tick n is queued, and only then waits for
+    tick n-1 to finish and hands out the results finished there (their
+    energies were queued into one of two pinned buffers before their
+    slots were retired).  The device always has the next tick queued while
+    the host does its bookkeeping."""
     from . import hsg
 
     sched = hsg.schedule(**sched_kw)
@@ -126,9 +143,11 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
     results: list[Result] = []
     ticks = max_batch = 0
     tuned = not autotune
+    prev = None  # the tick in flight: (marker, energy buffer or None, [(slot, request, admitted, spins)])
+    buf = 0
     with make_pool(budget_bytes, max_slots, stream) as pool:
         t0 = time.perf_counter()
-        while pending or waiting or active:
+        while pending or waiting or active or prev is not None:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
@@ -155,38 +174,46 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
                     raise
                 waiting.popleft()
                 active[slot] = [r, r.sweeps, time.perf_counter() - t0]
-            if not active:
+            cur = None
+            if active:
+                if not tuned and len(active) >= 8:
+                    hsg.hsg_pool_autotune(pool.pool, sched)
+                    tuned = True
+                k = min(tick_sweeps, min(a[1] for a in active.values()))
+                pool.sweep(sched, k)
+                ticks += 1
+                max_batch = max(max_batch, len(active))
+                done = []
+                for slot, a in active.items():
+                    a[1] -= k
+                    if a[1] == 0:
+                        done.append(slot)
+                finished = []
+                if done:
+                    pool.energies_async(buf)  # the finished lattices' final E/N, before their slots go
+                    for slot in done:
+                        r, _, t_adm = active.pop(slot)
+                        spins = pool.spins(slot) if keep_spins else None
+                        finished.append((slot, r, t_adm, spins))
+                        pool.retire(slot)
+                cur = (_marker(stream), buf if done else None, finished)
+                if done:
+                    buf ^= 1
+            elif prev is None:
                 if waiting:  # an empty pool refused it: it can never be admitted
                     rejected.append(waiting.popleft().rid)
                 elif pending:
                     time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
                 continue
-            if not tuned and len(active) >= 8:
-                hsg.hsg_pool_autotune(pool.pool, sched)
-                tuned = True
-            k = min(tick_sweeps, min(a[1] for a in active.values()))
-            pool.sweep(sched, k)
-            ticks += 1
-            max_batch = max(max_batch, len(active))
-            done = []
-            for slot, a in active.items():
-                a[1] -= k
-                if a[1] == 0:
-                    done.append(slot)
-            if done:
-                energies = pool.energies()  # synchronises: the finished lattices are final
-                t_done = time.perf_counter() - t0
-                for slot in done:
-                    r, _, t_adm = active.pop(slot)
-                    spins = pool.spins(slot) if keep_spins else None
-                    results.append(Result(r.rid, float(energies[slot]), r.arrival, t_adm, t_done, spins))
-                    pool.retire(slot)
-            elif stream is not None:
-                stream.synchronize()
-            else:
-                import torch
-
-                torch.cuda.synchronize()
+            if prev is not None:  # wait for the tick before this one and hand out its results
+                marker, b, finished = prev
+                marker.synchronize()
+                if finished:
+                    energies = pool.energies_read(b)
+                    t_done = time.perf_counter() - t0
+                    for slot, r, t_adm, spins in finished:
+                        results.append(Result(r.rid, float(energies[slot]), r.arrival, t_adm, t_done, spins))
+            prev = cur
         wall = time.perf_counter() - t0
     p50, p99, mean = latency_stats(results)
     by_id = {q.rid: q for q in requests}

@@ -187,3 +187,38 @@ def test_pool_admission_by_budget_and_slots(hsg):
         with pytest.raises(hsg.HsgError):
             pool.retire(7)  # no such slot
         assert len({b, c, d}) == 3
+
+
+def test_pool_energies_queued_before_a_retirement_survive_reuse_of_the_memory(hsg):
+    """hsg_pool_energies_async + hsg_pool_retire do not wait: a lattice's
+    E/N queued before its retirement is its final value even when a new
+    lattice is admitted into the freed block and swept before the read;
+    the new lattice is unaffected, and so is a lattice running alongside."""
+    kw = base_schedule(hsg, "MET")
+    per = 28 * 16 ** 3
+    with hsg.Pool(2 * per, 4, torch.cuda.Stream()) as pool:
+        a = pool.admit(16, 3, 0, 0, 0.5)
+        b = pool.admit(16, 3, 1, 0, 0.8)
+        pool.sweep(hsg.schedule(**kw), 4)
+        pool.energies_async(0)
+        pool.retire(a)
+        c = pool.admit(16, 3, 2, 0, 0.6)  # into a's block (the budget holds two)
+        pool.sweep(hsg.schedule(**kw), 3)
+        pool.energies_async(1)
+        pool.retire(b)
+        e0 = pool.energies_read(0)
+        e1 = pool.energies_read(1)
+        got_c = pool.spins(c)
+        _, ea = run_alone(hsg, (16, 3, 0, 0, 0.5), kw, 4)
+        _, eb4 = run_alone(hsg, (16, 3, 1, 0, 0.8), kw, 4)
+        _, eb7 = run_alone(hsg, (16, 3, 1, 0, 0.8), kw, 7)
+        want_c, ec = run_alone(hsg, (16, 3, 2, 0, 0.6), kw, 3)
+        assert abs(e0[a] - ea) <= 2e-6 and abs(e0[b] - eb4) <= 2e-6
+        assert abs(e1[b] - eb7) <= 2e-6 and abs(e1[c] - ec) <= 2e-6
+        assert np.array_equal(got_c, want_c)
+        assert math.isnan(e1[3]) and math.isnan(e0[2])  # free slots
+        for bad in (lambda: pool.energies_read(0),  # nothing queued any more
+                    lambda: pool.energies_async(2), lambda: hsg.hsg_pool_energies_read(pool.pool, -1, 4)):
+            with pytest.raises(hsg.HsgError) as err:
+                bad()
+            assert err.value.status == hsg.HSG_EINVAL

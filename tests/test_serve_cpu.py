@@ -76,13 +76,26 @@ class FakePool:
     def energies(self):
         return np.array([-self.slots[s][1] / 1000.0 if s in self.slots else np.nan for s in range(self.max_slots)])
 
+    def energies_async(self, buffer):
+        assert buffer in (0, 1) and buffer not in getattr(self, "queued", {})  # read before reuse
+        self.queued = getattr(self, "queued", {})
+        self.queued[buffer] = self.energies()
+
+    def energies_read(self, buffer):
+        return self.queued.pop(buffer)
+
     def spins(self, slot):
         return np.zeros(3 * self.slots[slot][0] ** 3, dtype=np.float32)
 
 
 class SyncStream:
+    """Stands in for a CUDA stream whose work is already done."""
+
     def synchronize(self):
         pass
+
+    def record_event(self):
+        return self
 
 
 def reqs(spec):
