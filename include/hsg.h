@@ -356,6 +356,12 @@ hsg_status hsg_pool_energies(hsg_pool* pool, double* out, int n);
 hsg_status hsg_pool_energies_async(hsg_pool* pool, int buffer);
 hsg_status hsg_pool_energies_read(hsg_pool* pool, int buffer, double* out, int n);
 
+/* As hsg_pool_energies_async for the n active slots listed in slots[]
+ * only (read back with hsg_pool_energies_read; every other slot reads
+ * NaN): the energy kernels skip the other lattices' sites.  A slot that is
+ * not active is HSG_EINVAL (nothing queued). */
+hsg_status hsg_pool_energies_slots_async(hsg_pool* pool, int buffer, const int* slots, int n);
+
 /* One lattice's spins, site-major fp32 (as hsg_get_spins), and counter. */
 hsg_status hsg_pool_get_spins(hsg_pool* pool, int slot, float* out, int where);
 hsg_status hsg_pool_get_sweep(hsg_pool* pool, int slot, uint64_t* sweep);

@@ -150,10 +150,12 @@ __global__ void __launch_bounds__(256) k_pool_energy_partial(const PoolDesc* __r
                                                              const uint2* __restrict__ tiles,
                                                              const uint32_t* __restrict__ n_tiles,
                                                              const float4* __restrict__ S, const float* __restrict__ J,
-                                                             uint32_t tile_sites, double* __restrict__ partials) {
+                                                             uint32_t tile_sites, const uint8_t* __restrict__ sel,
+                                                             double* __restrict__ partials) {
   const uint32_t nt = *n_tiles;
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const uint2 tl = tiles[t];
+    if (sel && !sel[tl.x]) continue;  // slot not asked for
     const PoolDesc* d = desc + tl.x;
     const uint32_t L = d->L, Lh = d->Lh, nh = d->nh, plane = d->plane;
     const float4* s0 = S + d->spin_off;
@@ -187,11 +189,12 @@ __global__ void __launch_bounds__(256) k_pool_energy_partial(const PoolDesc* __r
 // Energy, second pass: block per slot adds its tiles' partials in order;
 // E/N = -(sum)/N, NaN for inactive slots.
 __global__ void __launch_bounds__(256) k_pool_energy_final(const PoolDesc* __restrict__ desc, int n_slots,
+                                                           const uint8_t* __restrict__ sel,
                                                            const double* __restrict__ partials,
                                                            double* __restrict__ out) {
   for (int s = blockIdx.x; s < n_slots; s += gridDim.x) {
     const PoolDesc* d = desc + s;
-    if (!d->active) {
+    if (!d->active || (sel && !sel[s])) {
       if (threadIdx.x == 0) out[s] = __longlong_as_double(0x7ff8000000000000ll);
       continue;
     }
@@ -242,6 +245,11 @@ struct hsg_pool {
   // an event that its reader waits for.
   static constexpr int kEnergyBufs = 3;
   double* h_energy = nullptr;  // pinned, kEnergyBufs x max_slots
+  // Slots asked for by hsg_pool_energies_slots_async: a mask per buffer
+  // (pinned, kEnergyBufs x max_slots, free again once the buffer's event
+  // has passed) and the device copy the kernels read.
+  uint8_t* h_sel = nullptr;
+  uint8_t* d_sel = nullptr;
   cudaEvent_t en_ev[kEnergyBufs] = {nullptr, nullptr, nullptr};
   bool en_pending[kEnergyBufs] = {false, false, false};
   void* stage = nullptr;
@@ -483,6 +491,8 @@ hsg_status hsg_pool_create(hsg_pool** out, uint64_t budget_bytes, int max_slots,
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_ntiles, 2 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_energy, sizeof(double) * max_slots);
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_energy, hsg_pool::kEnergyBufs * sizeof(double) * max_slots);
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_sel, (size_t)hsg_pool::kEnergyBufs * max_slots);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_sel, (size_t)max_slots);
   for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->up_ev[i], cudaEventDisableTiming);
   for (int i = 0; i < hsg_pool::kEnergyBufs && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&p->en_ev[i], cudaEventDisableTiming);
@@ -513,6 +523,8 @@ hsg_status hsg_pool_destroy(hsg_pool* p) {
   cudaFree(p->d_partials);
   cudaFree(p->d_energy);
   cudaFreeHost(p->h_energy);
+  cudaFreeHost(p->h_sel);
+  cudaFree(p->d_sel);
   for (cudaEvent_t ev : p->up_ev)
     if (ev) cudaEventDestroy(ev);
   for (cudaEvent_t ev : p->en_ev)
@@ -650,23 +662,36 @@ hsg_status hsg_pool_sweep(hsg_pool* p, const hsg_schedule* sched, int n_sweeps) 
 
 namespace {
 
-// Queue the energy kernels of every slot and the copy of the result into
-// pinned buffer b, followed by b's event.
-hsg_status enqueue_energies(hsg_pool* p, int b) {
+// Queue the energy kernels and the copy of the result into pinned buffer
+// b, followed by b's event: every slot, or (slots != nullptr) the n listed
+// active slots only, the others reading NaN.
+hsg_status enqueue_energies(hsg_pool* p, int b, const int* slots = nullptr, int n = 0) {
+  if (slots)
+    for (int i = 0; i < n; ++i)
+      if (!valid_slot(p, slots[i])) return pfail(p, HSG_EINVAL, "no such active slot");
   hsg_status st = sync_tables(p);
   if (st != HSG_OK) return st;
   cudaError_t e = cudaSuccess;
   if (p->en_pending[b] && (e = cudaEventSynchronize(p->en_ev[b])) != cudaSuccess) return pcuda(p, e, "pool sync");
   p->en_pending[b] = false;
-  if (p->n_active > 0) {
+  const uint8_t* sel = nullptr;
+  if (slots) {  // the mask of buffer b is free: its last copy has passed
+    uint8_t* h = p->h_sel + (size_t)b * p->max_slots;
+    memset(h, 0, (size_t)p->max_slots);
+    for (int i = 0; i < n; ++i) h[slots[i]] = 1;
+    if ((e = cudaMemcpyAsync(p->d_sel, h, (size_t)p->max_slots, cudaMemcpyHostToDevice, p->stream)) != cudaSuccess)
+      return pcuda(p, e, "pool energies");
+    sel = p->d_sel;
+  }
+  if (p->n_active > 0 && (!slots || n > 0)) {
     k_pool_energy_partial<<<pool_grid(p), 256, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles,
                                                                 reinterpret_cast<const float4*>(p->arena),
                                                                 reinterpret_cast<const float*>(p->arena),
-                                                                (uint32_t)p->tile_sites, p->d_partials);
+                                                                (uint32_t)p->tile_sites, sel, p->d_partials);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    k_pool_energy_final<<<(unsigned)std::min(p->max_slots, 4096), 256, 0, p->stream>>>(p->d_desc, p->max_slots,
+    k_pool_energy_final<<<(unsigned)std::min(p->max_slots, 4096), 256, 0, p->stream>>>(p->d_desc, p->max_slots, sel,
                                                                                         p->d_partials, p->d_energy);
     e = cudaGetLastError();
   }
@@ -704,6 +729,14 @@ hsg_status hsg_pool_energies_async(hsg_pool* p, int buffer) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
   if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
   return enqueue_energies(p, buffer);
+}
+
+hsg_status hsg_pool_energies_slots_async(hsg_pool* p, int buffer, const int* slots, int n) {
+  if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
+  if (n < 0 || (n > 0 && !slots)) return pfail(p, HSG_EINVAL, "bad slot list");
+  static const int none = 0;
+  return enqueue_energies(p, buffer, n > 0 ? slots : &none, n);
 }
 
 hsg_status hsg_pool_energies_read(hsg_pool* p, int buffer, double* out, int n) {

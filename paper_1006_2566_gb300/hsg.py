@@ -100,6 +100,7 @@ _SIGS = {
     "hsg_pool_energies": ([_vp, ctypes.POINTER(_d), _i], _i),
     "hsg_pool_energies_async": ([_vp, _i], _i),
     "hsg_pool_energies_read": ([_vp, _i, ctypes.POINTER(_d), _i], _i),
+    "hsg_pool_energies_slots_async": ([_vp, _i, ctypes.POINTER(_i), _i], _i),
     "hsg_pool_get_spins": ([_vp, _i, _vp, _i], _i),
     "hsg_pool_get_sweep": ([_vp, _i, ctypes.POINTER(_u64)], _i),
     "hsg_pool_usage": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_i)], _i),
@@ -450,6 +451,12 @@ def hsg_pool_energies_async(pool, buffer: int) -> None:
     _pcheck(_lib.hsg_pool_energies_async(pool, int(buffer)), pool)
 
 
+def hsg_pool_energies_slots_async(pool, buffer: int, slots) -> None:
+    sl = np.ascontiguousarray(np.asarray(slots, dtype=np.int32).ravel())
+    _pcheck(_lib.hsg_pool_energies_slots_async(pool, int(buffer), sl.ctypes.data_as(ctypes.POINTER(_i)), sl.size),
+            pool)
+
+
 def hsg_pool_energies_read(pool, buffer: int, n: int) -> np.ndarray:
     out = np.zeros(int(n), dtype=np.float64)
     _pcheck(_lib.hsg_pool_energies_read(pool, int(buffer), out.ctypes.data_as(ctypes.POINTER(_d)), int(n)), pool)
@@ -536,9 +543,13 @@ class Pool:
     def energies(self) -> np.ndarray:
         return hsg_pool_energies(self.pool, self.max_slots)
 
-    def energies_async(self, buffer: int) -> None:
-        """Queue every slot's E/N into pinned buffer 0 or 1 (no wait)."""
-        hsg_pool_energies_async(self.pool, buffer)
+    def energies_async(self, buffer: int, slots=None) -> None:
+        """Queue the E/N of every slot, or of the listed slots only, into
+        pinned buffer 0 or 1 (no wait)."""
+        if slots is None:
+            hsg_pool_energies_async(self.pool, buffer)
+        else:
+            hsg_pool_energies_slots_async(self.pool, buffer, slots)
 
     def energies_read(self, buffer: int) -> np.ndarray:
         """Wait for the values queued into `buffer` and return them."""

@@ -190,7 +190,7 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
                         done.append(slot)
                 finished = []
                 if done:
-                    pool.energies_async(buf)  # the finished lattices' final E/N, before their slots go
+                    pool.energies_async(buf, done)  # the finished lattices' final E/N, before their slots go
                     for slot in done:
                         r, _, t_adm = active.pop(slot)
                         spins = pool.spins(slot) if keep_spins else None

@@ -217,8 +217,13 @@ def test_pool_energies_queued_before_a_retirement_survive_reuse_of_the_memory(hs
         assert abs(e1[b] - eb7) <= 2e-6 and abs(e1[c] - ec) <= 2e-6
         assert np.array_equal(got_c, want_c)
         assert math.isnan(e1[3]) and math.isnan(e0[2])  # free slots
+        # the finished slot alone: the same value, NaN elsewhere
+        pool.energies_async(0, [c])
+        e2 = pool.energies_read(0)
+        assert e2[c] == e1[c] and np.isnan(np.delete(e2, c)).all()
         for bad in (lambda: pool.energies_read(0),  # nothing queued any more
-                    lambda: pool.energies_async(2), lambda: hsg.hsg_pool_energies_read(pool.pool, -1, 4)):
+                    lambda: pool.energies_async(2), lambda: hsg.hsg_pool_energies_read(pool.pool, -1, 4),
+                    lambda: pool.energies_async(0, [b])):  # b is retired
             with pytest.raises(hsg.HsgError) as err:
                 bad()
             assert err.value.status == hsg.HSG_EINVAL

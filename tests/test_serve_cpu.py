@@ -76,10 +76,13 @@ class FakePool:
     def energies(self):
         return np.array([-self.slots[s][1] / 1000.0 if s in self.slots else np.nan for s in range(self.max_slots)])
 
-    def energies_async(self, buffer):
+    def energies_async(self, buffer, slots=None):
         assert buffer in (0, 1) and buffer not in getattr(self, "queued", {})  # read before reuse
         self.queued = getattr(self, "queued", {})
-        self.queued[buffer] = self.energies()
+        e = self.energies()
+        if slots is not None:
+            e[[s for s in range(self.max_slots) if s not in slots]] = np.nan
+        self.queued[buffer] = e
 
     def energies_read(self, buffer):
         return self.queued.pop(buffer)
