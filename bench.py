@@ -259,7 +259,7 @@ def step_bytes(wl, wave: bool = False, packed: bool = False) -> int:
     extra = 0
     if wl["energy_every"]:
         extra += n * b_en * (s // wl["energy_every"])
-    if wl["renorm_every"]:
+    if wl["renorm_every"] and not (wave and wl["n_or"] > 0):  # else fused into the last wave sweep
         extra += n * b_rn * (s // wl["renorm_every"])
     return per_sweep * s + extra
 
@@ -458,6 +458,10 @@ def run_ours(args, wl):
                    (BYTES_RENORM_PACKED if packed else BYTES_RENORM))
             kernels[name] = {"avg_ms": round(ms / n, 5), "launches": n,
                              "GBps": round(N * bpu / (ms / n / 1e3) / 1e9, 1)}
+    ms, n = per_class[hsg.HSG_PROF_OVERRELAX_RENORM]
+    if n:  # the last wave sweep before a renormalisation, renormalising as it stores (same bytes, FP64 work)
+        kernels["overrelax_renorm"] = {"avg_ms": round(ms / n, 5), "launches": n,
+                                       "GBps": round(N * BYTES_OR_WAVE / (ms / n / 1e3) / 1e9, 1)}
     step_gbps = step_bytes(wl, wave, packed) / (elapsed_ms / args.steps / 1e3) / 1e9
     out = {
         "metric": "spin updates/ns", "value": round(value, 4), "unit": "spin updates/ns", "n_gpus": world,

@@ -106,7 +106,9 @@ enum {
   HSG_PROF_HEATBATH = 4,
   HSG_PROF_ENERGY = 5,   /* both energy kernels */
   HSG_PROF_RENORM = 6,
-  HSG_PROF_COUNT = 7
+  HSG_PROF_OVERRELAX_RENORM = 7, /* an over-relaxation wave sweep that also renormalises what it stores
+                                  * (a renormalisation due right after it, fused into it) */
+  HSG_PROF_COUNT = 8
 };
 
 /*

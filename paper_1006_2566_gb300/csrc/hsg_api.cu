@@ -285,15 +285,17 @@ hsg_status run_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int col
 }
 
 // Both colours of one over-relaxation sweep in one temporally blocked launch
-// from c->spins into c->spins_alt; then the two buffers swap.
-hsg_status run_or_sweep_wave(hsg_ctx* c) {
+// from c->spins into c->spins_alt (renormalising what it stores when
+// `renorm`); then the two buffers swap.
+hsg_status run_or_sweep_wave(hsg_ctx* c, bool renorm) {
   hsg::WaveArgs a{};
   a.src = c->spins;
   a.dst = c->spins_alt;
   a.J = c->J;
   a.L = c->L;
   a.Lh = c->Lh;
-  hsg_status st = launch(c, HSG_PROF_OVERRELAX, 1, "over-relaxation sweep kernel",
+  a.renorm = renorm;
+  hsg_status st = launch(c, renorm ? HSG_PROF_OVERRELAX_RENORM : HSG_PROF_OVERRELAX, 1, "over-relaxation sweep kernel",
                          [&] { return hsg::launch_or_sweep_wave(a, c->sm_count, c->stream); });
   if (st == HSG_OK) std::swap(c->spins, c->spins_alt);
   return st;
@@ -323,9 +325,14 @@ hsg_status enqueue_one_sweep(hsg_ctx* c, const hsg_schedule* s) {
   if (s->kind != HSG_NONE)
     for (int colour = 0; colour < 2; ++colour)
       if ((st = run_half_sweep(c, s, s->kind, colour)) != HSG_OK) return st;
+  // A renormalisation due after this sweep is fused into its last wave
+  // launch (the same renorm_spin on the same values; the counter kernel in
+  // between touches no spin).
+  const bool renorm_due = s->renorm_every > 0 && (c->sweep + 1) % (uint64_t)s->renorm_every == 0;
+  const bool fuse_renorm = renorm_due && wave && s->n_or > 0;
   for (int o = 0; o < s->n_or; ++o) {
     if (wave) {
-      if ((st = run_or_sweep_wave(c)) != HSG_OK) return st;
+      if ((st = run_or_sweep_wave(c, fuse_renorm && o == s->n_or - 1)) != HSG_OK) return st;
       continue;
     }
     for (int colour = 0; colour < 2; ++colour)
@@ -333,7 +340,7 @@ hsg_status enqueue_one_sweep(hsg_ctx* c, const hsg_schedule* s) {
   }
   if ((st = run_advance(c)) != HSG_OK) return st;
   c->sweep += 1;
-  if (s->renorm_every > 0 && c->sweep % (uint64_t)s->renorm_every == 0)
+  if (renorm_due && !fuse_renorm)
     if ((st = run_renorm(c)) != HSG_OK) return st;
   if (s->energy_every > 0 && c->sweep % (uint64_t)s->energy_every == 0) {
     if ((st = run_energy(c, c->elog, true)) != HSG_OK) return st;

@@ -46,10 +46,12 @@ struct WaveArgs {
   float4* dst;        // S[2][N/2] after the sweep; must not overlap src
   const float* J;     // J[3][2][N/2]
   int L, Lh;
+  bool renorm;  // store every new spin renormalised (renorm_spin)
 };
 
 // Over-relaxation sweep (both colours) in one launch, bit-identical to the
-// colour-0 and colour-1 half-sweeps of launch_half_sweep(U_OR, ...).
+// colour-0 and colour-1 half-sweeps of launch_half_sweep(U_OR, ...), and
+// with `renorm` set to those half-sweeps followed by launch_renorm.
 cudaError_t launch_or_sweep_wave(const WaveArgs& a, int sm_count, cudaStream_t s);
 
 // Spin layouts (hsg_device.cuh): `packed` = three fp32 component arrays per

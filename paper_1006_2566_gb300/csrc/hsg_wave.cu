@@ -122,6 +122,11 @@ __device__ __forceinline__ SiteBonds load_bonds(const float* __restrict__ jc, co
   return b;
 }
 
+// RENORM: the stored spins are renormalised (renorm_spin), as by a
+// renormalisation pass right after the sweep; the colour-0 values that
+// stage 1 reads from shared memory are the unrenormalised ones, as in the
+// unfused order.
+template <bool RENORM>
 __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const WaveArgs a, int zc) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   WaveSmem& sm = *reinterpret_cast<WaveSmem*>(smem_raw);
@@ -249,7 +254,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
       in.site = 0;  // over-relaxation draws no random numbers
       const float4 v = site_result<U_OR>(in, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
       c0s[c0p][t] = v;
-      if (owned0 && s >= 1 && s <= z1 - z0) dst0[z * plane + o0.off] = v;
+      if (owned0 && s >= 1 && s <= z1 - z0) dst0[z * plane + o0.off] = RENORM ? renorm_spin(v) : v;
       float(*jb)[R0N] = sm.jb[(s + 1) & 1];
       jb[B_XP][t] = cb0.xp;
       jb[B_YP][t] = cb0.yp;
@@ -291,7 +296,8 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
       in.s = make_float3(o.x, o.y, o.z);
       in.q = 0;
       in.site = 0;
-      dst1[z * plane + off1] = site_result<U_OR>(in, 1u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
+      const float4 r = site_result<U_OR>(in, 1u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
+      dst1[z * plane + off1] = RENORM ? renorm_spin(r) : r;
     }
     if (s >= 1 && valid1) jzm1 = jb[B_ZP][b0];
     bm = bc;
@@ -304,7 +310,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
 
 // Launch shape, measured at L = 256 (OR sweep time; bit-identical results
 // in every case):
-//  * carveout hint 58 %: the driver takes the next supported configuration,
+//  * carveout hint 58 %: the CUDA driver takes the next supported configuration,
 //    164 KB of shared memory -- the smallest that holds three 51 KB CTAs --
 //    and leaves 92 KB of the SM's unified array as L1 for the in-flight bond
 //    loads of stage 0: 166 us.  With 60 KB of L1 left (196 KB shared) 178 us,
@@ -315,16 +321,24 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
 constexpr int W_CARVEOUT_PCT = 58;
 constexpr int W_GRID_PER_SM = 3;
 
-cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
+template <bool RENORM>
+cudaError_t configure_wave() {
   static bool configured = false;
   if (!configured) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_or_sweep_wave, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM);
+        cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_or_sweep_wave, cudaFuncAttributePreferredSharedMemoryCarveout, W_CARVEOUT_PCT);
+      e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               W_CARVEOUT_PCT);
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
+  const cudaError_t e = a.renorm ? configure_wave<true>() : configure_wave<false>();
+  if (e != cudaSuccess) return e;
   const unsigned tx = cdiv(a.Lh, WX), ty = cdiv(a.L, WY);
   long long chunks = (long long)W_GRID_PER_SM * sm_count / ((long long)tx * ty);
   if (chunks < 1) chunks = 1;
@@ -332,7 +346,10 @@ cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
   if (zc < MIN_ZC) zc = MIN_ZC;
   if (zc > a.L) zc = a.L;
   const dim3 grid(tx, ty, cdiv(a.L, zc));
-  k_or_sweep_wave<<<grid, W_THREADS, W_SMEM, s>>>(a, zc);
+  if (a.renorm)
+    k_or_sweep_wave<true><<<grid, W_THREADS, W_SMEM, s>>>(a, zc);
+  else
+    k_or_sweep_wave<false><<<grid, W_THREADS, W_SMEM, s>>>(a, zc);
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ HSG_HOST, HSG_DEVICE = 0, 1
 HSG_KERNEL_AUTO, HSG_KERNEL_GLOBAL, HSG_KERNEL_SLAB, HSG_KERNEL_WAVE = 0, 1, 2, 3
 HSG_LAYOUT_FLOAT4, HSG_LAYOUT_PACKED = 0, 1
 (HSG_PROF_INIT, HSG_PROF_LAYOUT, HSG_PROF_OVERRELAX, HSG_PROF_METROPOLIS, HSG_PROF_HEATBATH,
- HSG_PROF_ENERGY, HSG_PROF_RENORM, HSG_PROF_COUNT) = range(8)
+ HSG_PROF_ENERGY, HSG_PROF_RENORM, HSG_PROF_OVERRELAX_RENORM, HSG_PROF_COUNT) = range(9)
 
 
 class HsgError(RuntimeError):

@@ -209,3 +209,21 @@ def test_auto_picks_the_wave_kernel_only_beyond_l2(hsg):
             assert hsg.hsg_kernel_for(lat.ctx, sched) == want
             for k in (hsg.HSG_KERNEL_GLOBAL, hsg.HSG_KERNEL_SLAB, hsg.HSG_KERNEL_WAVE):
                 assert hsg.hsg_kernel_for(lat.ctx, hsg.schedule(n_or=1, kernel=k)) == k
+
+
+def test_wave_fuses_the_renormalisation_into_the_last_over_relaxation_sweep(hsg):
+    """With the wave kernel a renormalisation due after a sweep is done by
+    that sweep's last over-relaxation launch (no launch of its own); with
+    half-sweeps it stays a launch.  Results are the same bit for bit (the
+    tests above run renormalising schedules on both kernels)."""
+    L = 32
+    counts = {}
+    for kernel in (hsg.HSG_KERNEL_WAVE, hsg.HSG_KERNEL_GLOBAL):
+        with hsg.Lattice(L, 1) as lat:
+            lat.generate_couplings()
+            hsg.hsg_profile(lat.ctx, 1)
+            lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, T=0.3, n_or=2, renorm_every=2, kernel=kernel), 4)
+            counts[kernel] = [hsg.hsg_profile_read(lat.ctx, k)[1]
+                              for k in (hsg.HSG_PROF_OVERRELAX, hsg.HSG_PROF_OVERRELAX_RENORM, hsg.HSG_PROF_RENORM)]
+    assert counts[hsg.HSG_KERNEL_WAVE] == [6, 2, 0]  # the last OR sweep of sweeps 2 and 4 renormalises
+    assert counts[hsg.HSG_KERNEL_GLOBAL] == [16, 0, 2]
