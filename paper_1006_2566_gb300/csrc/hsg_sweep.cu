@@ -6,6 +6,8 @@
 // Two variants over the colour-split layout of hsg_device.cuh:
 //   global : one thread per updated site; the six neighbours come through
 //            L1/L2 (the lattice is streamed once per half-sweep from HBM).
+//            Its heat-bath launches march a thread up a short column of
+//            planes instead (k_half_sweep_column).
 //   slab   : a CTA owns a (32 xh) x (8 y) column tile and marches up a chunk
 //            of z planes.  The other colour's plane z (with a one-site halo)
 //            is staged in shared memory for the x and y neighbours; planes
@@ -30,10 +32,10 @@ __device__ __forceinline__ uint32_t site_number(int xh, int p, int y, int z, int
 // ---------------------------------------------------------------------------
 constexpr int G_THREADS = 128;
 
-// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.  The over-relaxation and
-// heat-bath kernels are held to 32 registers so that 16 blocks (full
-// occupancy) fit on an SM (measured at L = 256: OR 92 us at 32 registers vs
-// 99 us at 36-40); Metropolis, which would spill, keeps its registers.
+// Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.  The over-relaxation
+// kernel is held to 32 registers so that 16 blocks (full occupancy) fit on
+// an SM (measured at L = 256: OR 92 us at 32 registers vs 99 us at 36-40);
+// Metropolis, which would spill, keeps its registers.
 template <int U>
 __global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
     k_half_sweep_global(const SweepArgs a) {
@@ -52,6 +54,73 @@ __global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
   }
   half_sweep_site<U>(a.own, a.oth, a.jx_own, a.jy_own, a.jz_own, a.jx_oth, a.jy_oth, a.jz_oth, xh, y, z, L, Lh,
                      (uint32_t)a.colour, sweep_lo, sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
+}
+
+// Heat-bath half-sweeps of the global variant: one thread per (xh, y)
+// column of the updated colour over ZM_PLANES consecutive planes.  The
+// other colour's spins in the thread's own column on planes z-1 and z (the
+// site's -z neighbour and one of its x neighbours) are carried from the
+// plane before, so a site loads four neighbour spins instead of six; the
+// inputs and the site code are those of k_half_sweep_global, so the results
+// are the same bit for bit.  Measured on the L = 256 heat-bath half-sweep:
+// 6 planes and 40 registers (12 blocks per SM) 94.0 us, against 100.9 us
+// for one site per thread at 32 registers; 8 planes 95.1, 4 planes 96.0,
+// 16 planes 97.3, 32 planes 107; at 32 registers (spilling) 104-106 us.
+constexpr int ZM_PLANES = 6;
+
+template <int U>
+__global__ void __launch_bounds__(G_THREADS, 12) k_half_sweep_column(const SweepArgs a) {
+  const uint32_t xh = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
+  const uint32_t L = a.L, Lh = a.Lh;
+  if (xh >= Lh || y >= L) return;
+  uint32_t sweep_lo = a.sweep_lo, sweep_hi = a.sweep_hi;
+  if (a.sweep_ptr) {
+    const unsigned long long sw = *a.sweep_ptr;
+    sweep_lo = (uint32_t)sw;
+    sweep_hi = (uint32_t)(sw >> 32);
+  }
+  const uint32_t plane = L * Lh;
+  const uint32_t z0 = blockIdx.z * ZM_PLANES, z1 = min(z0 + ZM_PLANES, L);
+  // rows y, y+1, y-1 and columns xh+1, xh-1, wrapped (the layout comment of
+  // hsg_device.cuh; the same indices as site_index)
+  const uint32_t row = y * Lh, row_p = (y + 1 == L ? 0u : y + 1) * Lh, row_m = (y == 0 ? L - 1 : y - 1) * Lh;
+  const uint32_t xm1 = xh == 0 ? Lh - 1 : xh - 1, xp1 = xh + 1 == Lh ? 0u : xh + 1;
+  const float4* __restrict__ oth = a.oth;
+  uint32_t zmo = (z0 == 0 ? L - 1 : z0 - 1) * plane, zo = z0 * plane;
+  float4 s_m = __ldg(oth + zmo + row + xh), s_0 = __ldg(oth + zo + row + xh);
+  for (uint32_t z = z0; z < z1; ++z) {
+    const uint32_t zpo = z + 1 == L ? 0u : zo + plane;
+    const uint32_t p = ((uint32_t)a.colour + y + z) & 1u;  // x = 2 xh + p
+    const uint32_t q = zo + row + xh;
+    const float4 s_p = __ldg(oth + zpo + row + xh);
+    const float4 side = __ldg(oth + zo + row + (p ? xp1 : xm1));
+    SiteInputs in;
+    in.sxp = p ? side : s_0;
+    in.sxm = p ? s_0 : side;
+    in.syp = __ldg(oth + zo + row_p + xh);
+    in.sym = __ldg(oth + zo + row_m + xh);
+    in.szp = s_p;
+    in.szm = s_m;
+    in.jxp = __ldg(a.jx_own + q);
+    in.jxm = __ldg(a.jx_oth + (p ? q : zo + row + xm1));
+    in.jyp = __ldg(a.jy_own + q);
+    in.jym = __ldg(a.jy_oth + zo + row_m + xh);
+    in.jzp = __ldg(a.jz_own + q);
+    in.jzm = __ldg(a.jz_oth + zmo + row + xh);
+    in.s = make_float3(0.0f, 0.0f, 0.0f);
+    if constexpr (U != U_HB) {
+      const float4 o = a.own[q];
+      in.s = make_float3(o.x, o.y, o.z);
+    }
+    in.q = q;
+    in.site = (2 * xh + p) + y * L + z * L * L;
+    a.own[q] = site_result<U>(in, (uint32_t)a.colour, sweep_lo, sweep_hi, a.k0, a.k1, a.beta, a.step, a.hits);
+    s_m = s_0;
+    s_0 = s_p;
+    zmo = zo;
+    zo = zpo;
+  }
 }
 
 // The global variant over the packed layout (three fp32 arrays per colour,
@@ -163,7 +232,12 @@ cudaError_t launch_kind(int variant, const SweepArgs& a, cudaStream_t s) {
   } else {
     const dim3 block = a.Lh >= 64 ? dim3(64, 2) : dim3(32, 4);
     const dim3 grid(cdiv(a.Lh, block.x), cdiv(a.L, block.y), (unsigned)a.L);
-    k_half_sweep_global<U><<<grid, block, 0, s>>>(a);
+    if constexpr (U == U_HB) {
+      const dim3 gcol(grid.x, grid.y, cdiv(a.L, ZM_PLANES));
+      k_half_sweep_column<U><<<gcol, block, 0, s>>>(a);
+    } else {
+      k_half_sweep_global<U><<<grid, block, 0, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -295,7 +295,7 @@ def test_heatbath_half_sweep_parity(hsg, variant, L, T):
         assert np.max(np.abs(np.linalg.norm(got.reshape(-1, 3)[mask], axis=1) - 1)) < 1e-5
 
 
-@pytest.mark.parametrize("L", [8, 40])
+@pytest.mark.parametrize("L", [4, 8, 14, 40, 66])  # the heat-bath column march: shorter than, and ragged in, its 6-plane chunks
 def test_kernel_variants_are_bit_identical(hsg, L):
     J = inputs.gaussian_couplings(L, seed=3)
     out = []
