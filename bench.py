@@ -519,10 +519,11 @@ def _oracle_sample_sweep(oracle, L, J, s, kind, p, i0, i1):
     return n
 
 
-def cpu_baseline(wl):
-    """One full sweep of the workload's lattice by the FP64 oracle on one
-    thread (about 6-20 s), and one on every host core (the oracle's OpenMP
-    half-sweep loop; the same arithmetic)."""
+def cpu_baseline(wl, target_s: float = 10.0):
+    """Full sweeps of the workload's lattice by the FP64 oracle on one
+    thread -- as many as it takes to pass target_s seconds (two at L = 256
+    on a Grace core, about 12 s) -- and one on every host core (the oracle's
+    OpenMP half-sweep loop; the same arithmetic)."""
     oracle, L, J, s, kind, p = _oracle_setup(wl)
     N = L ** 3
 
@@ -535,9 +536,14 @@ def cpu_baseline(wl):
             updates += N
         return updates, time.perf_counter() - t
 
-    updates, dt = sweep()
+    updates = n_sweeps = 0
+    dt = 0.0
+    while dt < target_s:
+        u, t = sweep()
+        updates, dt, n_sweeps = updates + u, dt + t, n_sweeps + 1
     out = {"value": round(updates / (dt * 1e9), 6), "unit": "spin updates/ns", "cores": 1, "kind": "oracle",
-           "sample": f"1 full sweep (main update + {wl['n_or']} OR) of the L={L} lattice, fp64, 1 thread",
+           "sample": f"{n_sweeps} full sweep(s) (main update + {wl['n_or']} OR) of the L={L} lattice, fp64, "
+                     f"1 thread, until {target_s:.0f} s had passed",
            "seconds": round(dt, 2)}
     cores = oracle.max_threads()
     if cores > 1:
