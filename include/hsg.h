@@ -76,7 +76,9 @@ enum {
   HSG_KERNEL_AUTO = 0,   /* library's choice: HSG_KERNEL_WAVE when the lattice's
                           * spins and bonds (28 N bytes) exceed the device's L2,
                           * so that the sweep streams from HBM; else GLOBAL */
-  HSG_KERNEL_GLOBAL = 1, /* one thread per site, neighbours through L1/L2 */
+  HSG_KERNEL_GLOBAL = 1, /* one thread per site, neighbours through L1/L2 (heat-bath:
+                          * one thread per six-plane column, carrying its column's
+                          * neighbours; the same results) */
   HSG_KERNEL_SLAB = 2,   /* z-marching tiles: other colour staged in shared memory */
   /* Temporally blocked over-relaxation: each over-relaxation sweep
    * runs colour 0 and colour 1 in ONE pass over the lattice (z-marching
@@ -86,7 +88,9 @@ enum {
    * are bit-identical to HSG_KERNEL_GLOBAL.  The pass writes a second spin
    * buffer of 16 N bytes, allocated by the first hsg_sweep that needs it and
    * kept until hsg_destroy; the two buffers alternate.  The main update of a
-   * sweep and hsg_half_sweep use the global kernel. */
+   * sweep and hsg_half_sweep use the global kernel.  A renormalisation due
+   * right after a sweep is done by that sweep's last wave pass, as it
+   * stores (bit-identical to a renormalisation of its own). */
   HSG_KERNEL_WAVE = 3
 };
 
