@@ -642,7 +642,7 @@ def run_batched(args):
             pool.admit(*spec)
         t0 = time.perf_counter()
         if args.no_autotune:
-            cfg = (256, 512, 8)  # the pool's default launch configuration
+            cfg = (256, 512, 8, 0)  # the pool's default launch configuration
             hsg.hsg_pool_config(pool.pool, *cfg)
         else:
             cfg = hsg.hsg_pool_autotune(pool.pool, sched)
@@ -691,6 +691,7 @@ def run_batched(args):
         "data": "synthetic: seeded sides and temperatures, couplings and spins from Philox",
         "config": {"workload": BATCH["desc"], "lattices": len(specs), "sites": sites,
                    "autotuned": {"threads": cfg[0], "tile_sites": cfg[1], "blocks_per_sm": cfg[2],
+                                 "hits_per_pass": cfg[3] or BATCH["hits"],
                                  "seconds": round(tune_s, 3)}},
         "hit_updates_per_ns": round(sites * (BATCH["hits"] + BATCH["n_or"]) * sps * args.steps / (ms * 1e6), 4),
         "plain_one_lattice_per_launch": {"value": round(plain, 4), "unit": "spin updates/ns",

@@ -376,14 +376,23 @@ hsg_status hsg_pool_get_sweep(hsg_pool* pool, int slot, uint64_t* sweep);
 hsg_status hsg_pool_usage(hsg_pool* pool, uint64_t* bytes_used, uint64_t* bytes_budget, int* active);
 
 /* Launch configuration of the pool kernels: threads per CTA (64, 128 or
- * 256), sites per tile (a multiple of threads, <= 8192) and CTAs per SM of
- * the persistent grid (1..32).  hsg_pool_autotune times every candidate on
- * the admitted lattices (one warm-up and two timed sweeps each), restores
- * the lattices and counters afterwards, keeps the fastest configuration and
- * reports it.  Results do not depend on the configuration. */
-hsg_status hsg_pool_config(hsg_pool* pool, int threads, int tile_sites, int blocks_per_sm);
+ * 256), sites per tile (a multiple of threads, <= 8192), CTAs per SM of the
+ * persistent grid (1..32), and Metropolis hits per pass (0: all of a
+ * colour's hits in one pass; h > 0: the hits in passes of at most h, each a
+ * launch that reads and writes the colour again -- the neighbours are fixed
+ * for the whole half-sweep and hit j draws the Philox numbers keyed by j,
+ * so the result is the same; Table 3 of the paper runs the hits in one
+ * pass).  hsg_pool_autotune times every launch shape with all hits in one
+ * pass, then the best shape with 1, 2, 4, ... hits per pass (Metropolis
+ * schedules with more than one hit), on the admitted lattices (one warm-up
+ * and two timed sweeps each), restores the lattices and counters
+ * afterwards, keeps the fastest configuration and reports it.  Results do
+ * not depend on the configuration.  Errors: HSG_EINVAL (NULL pool, values
+ * out of range; autotune with no lattice admitted or on the legacy default
+ * stream). */
+hsg_status hsg_pool_config(hsg_pool* pool, int threads, int tile_sites, int blocks_per_sm, int hits_per_pass);
 hsg_status hsg_pool_autotune(hsg_pool* pool, const hsg_schedule* schedule, int* threads, int* tile_sites,
-                             int* blocks_per_sm);
+                             int* blocks_per_sm, int* hits_per_pass);
 
 /* Kernel launches issued for this pool (graph replays count their kernels). */
 hsg_status hsg_pool_launch_count(hsg_pool* pool, uint64_t* launches);

@@ -85,8 +85,11 @@ __device__ __forceinline__ float3 sphere_point_fast(float u0, float u1) {
   return make_float3(-rho * c, -rho * s, z);
 }
 
-// Multi-hit Metropolis at fixed field h.  Hit j uses the Philox draw at
-// counter (site, sweep_lo, MET<<24 | colour<<16 | j, sweep_hi).  The site
+// Multi-hit Metropolis at fixed field h: hits hit0 .. hit0 + hits - 1 (a
+// colour's hits may be split over several passes: the field is fixed for
+// the whole half-sweep, so the result does not depend on the split).  Hit
+// j uses the Philox draw at counter (site, sweep_lo, MET<<24 | colour<<16 | j,
+// sweep_hi).  The site
 // energy in the field is -s.h, dE = -(s' - s).h, accept iff u3 < exp(-beta dE).
 // The proposal uses the fast sphere point, the ball radius cbrt(u2) is
 // __powf(u2, 1/3) (relative error ~1e-6 for u2 in (0,1)), the normalisation
@@ -95,8 +98,8 @@ __device__ __forceinline__ float3 sphere_point_fast(float u0, float u1) {
 template <bool BALL>
 __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t site, uint32_t colour,
                                                     uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
-                                                    uint32_t k1, float beta, float step, int hits) {
-  for (int j = 0; j < hits; ++j) {
+                                                    uint32_t k1, float beta, float step, int hits, int hit0 = 0) {
+  for (int j = hit0; j < hit0 + hits; ++j) {
     const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_MET << 24) | (colour << 16) | (uint32_t)j,
                                              sweep_hi),
                                   k0, k1);
@@ -184,17 +187,19 @@ __device__ __forceinline__ float3 local_field(float4 sxp, float4 sxm, float4 syp
 template <int U>
 __device__ __forceinline__ float3 update_site(float3 s, float3 h, uint32_t site, uint32_t colour, uint32_t sweep_lo,
                                               uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta, float step,
-                                              int hits) {
+                                              int hits, int hit0 = 0) {
   if constexpr (U == U_OR) {
     return update_or(s, h);
   } else if constexpr (U == U_MET_SPHERE) {
-    return update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+    return update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0);
   } else if constexpr (U == U_MET_BALL) {
-    return update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+    return update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0);
   } else if constexpr (U == U_MET_OR_SPHERE) {
-    return update_or(update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits), h);
+    return update_or(
+        update_metropolis<false>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0), h);
   } else if constexpr (U == U_MET_OR_BALL) {
-    return update_or(update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits), h);
+    return update_or(
+        update_metropolis<true>(s, h, site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0), h);
   } else {
     return update_heatbath(h, site, colour, sweep_lo, sweep_hi, k0, k1, beta);
   }
@@ -332,10 +337,10 @@ __device__ __forceinline__ void gather_site(SiteInputs& in, const float4* __rest
 template <int U>
 __device__ __forceinline__ float4 site_result(const SiteInputs& in, uint32_t colour, uint32_t sweep_lo,
                                               uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta, float step,
-                                              int hits) {
+                                              int hits, int hit0 = 0) {
   const float3 h = local_field(in.sxp, in.sxm, in.syp, in.sym, in.szp, in.szm, in.jxp, in.jxm, in.jyp, in.jym,
                                in.jzp, in.jzm);
-  const float3 t = update_site<U>(in.s, h, in.site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  const float3 t = update_site<U>(in.s, h, in.site, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0);
   return make_float4(t.x, t.y, t.z, 0.0f);
 }
 
@@ -343,8 +348,8 @@ __device__ __forceinline__ float4 site_result(const SiteInputs& in, uint32_t col
 template <int U>
 __device__ __forceinline__ void finish_site(const SiteInputs& in, float4* __restrict__ own, uint32_t colour,
                                             uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0, uint32_t k1,
-                                            float beta, float step, int hits) {
-  own[in.q] = site_result<U>(in, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+                                            float beta, float step, int hits, int hit0 = 0) {
+  own[in.q] = site_result<U>(in, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0);
 }
 
 // One site of a half-sweep: gather, then finish.  Every half-sweep kernel
@@ -357,10 +362,10 @@ __device__ __forceinline__ void half_sweep_site(float4* __restrict__ own, const 
                                                 const float* __restrict__ jy_oth, const float* __restrict__ jz_oth,
                                                 uint32_t xh, uint32_t y, uint32_t z, uint32_t L, uint32_t Lh,
                                                 uint32_t colour, uint32_t sweep_lo, uint32_t sweep_hi, uint32_t k0,
-                                                uint32_t k1, float beta, float step, int hits) {
+                                                uint32_t k1, float beta, float step, int hits, int hit0 = 0) {
   SiteInputs in;
   gather_site<U>(in, own, oth, jx_own, jy_own, jz_own, jx_oth, jy_oth, jz_oth, xh, y, z, L, Lh, colour);
-  finish_site<U>(in, own, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits);
+  finish_site<U>(in, own, colour, sweep_lo, sweep_hi, k0, k1, beta, step, hits, hit0);
 }
 
 // One site of a half-sweep in the packed layout (same arithmetic).

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(256, 4) k_pool_half_sweep(const PoolDesc* __re
                                                          const uint2* __restrict__ tiles,
                                                          const uint32_t* __restrict__ n_tiles, float4* __restrict__ S,
                                                          const float* __restrict__ J, uint32_t colour, float step,
-                                                         int hits, uint32_t tile_sites) {
+                                                         int hits, int hit0, uint32_t tile_sites) {
   const uint32_t nt = *n_tiles;
   for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {
     const uint2 tl = tiles[t];
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, 4) k_pool_half_sweep(const PoolDesc* __re
       uint32_t xh, y, z;
       decode_site(d, q, xh, y, z);
       hsg::half_sweep_site<U>(own, oth, jxo, jyo, jzo, jxt, jyt, jzt, xh, y, z, L, Lh, colour, d->sweep_lo,
-                              d->sweep_hi, d->k0, d->k1, d->beta, step, hits);
+                              d->sweep_hi, d->k0, d->k1, d->beta, step, hits, hit0);
     }
   }
 }
@@ -256,8 +256,10 @@ struct hsg_pool {
   size_t stage_bytes = 0;
   bool dirty = true;
   int threads = 256, tile_sites = 512, blocks_per_sm = 8;
+  // Metropolis hits per pass over a colour (0: all of them in one pass).
+  int hits_per_pass = 0;
   struct GraphKey {
-    int kind, hits, proposal, n_or, renorm_every, threads, tile_sites, bps;
+    int kind, hits, proposal, n_or, renorm_every, threads, tile_sites, bps, hits_per_pass;
     float step;
     bool operator==(const GraphKey& o) const { return memcmp(this, &o, sizeof(GraphKey)) == 0; }
   };
@@ -405,22 +407,44 @@ hsg_status sync_tables(hsg_pool* p) {
 
 unsigned pool_grid(const hsg_pool* p) { return (unsigned)(p->sm_count * p->blocks_per_sm); }
 
-cudaError_t launch_pool_half(hsg_pool* p, int upd, uint32_t colour, float step, int hits) {
+cudaError_t launch_pool_half(hsg_pool* p, int upd, uint32_t colour, float step, int hits, int hit0) {
   const dim3 g(pool_grid(p)), b(p->threads);
   const float4* S4 = reinterpret_cast<const float4*>(p->arena);
   float4* S = const_cast<float4*>(S4);
   const float* J = reinterpret_cast<const float*>(p->arena);
   const uint32_t ts = (uint32_t)p->tile_sites;
+  const PoolDesc* D = p->d_desc;
+  const uint2* T = p->d_tiles;
+  const uint32_t* NT = p->d_ntiles;
+  cudaStream_t st = p->stream;
   switch (upd) {
-    case hsg::U_OR: k_pool_half_sweep<hsg::U_OR><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
-    case hsg::U_MET_SPHERE: k_pool_half_sweep<hsg::U_MET_SPHERE><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
-    case hsg::U_MET_BALL: k_pool_half_sweep<hsg::U_MET_BALL><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
-    case hsg::U_MET_OR_SPHERE: k_pool_half_sweep<hsg::U_MET_OR_SPHERE><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
-    case hsg::U_MET_OR_BALL: k_pool_half_sweep<hsg::U_MET_OR_BALL><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
-    default: k_pool_half_sweep<hsg::U_HB><<<g, b, 0, p->stream>>>(p->d_desc, p->d_tiles, p->d_ntiles, S, J, colour, step, hits, ts); break;
+    case hsg::U_OR: k_pool_half_sweep<hsg::U_OR><<<g, b, 0, st>>>(D, T, NT, S, J, colour, step, hits, hit0, ts); break;
+    case hsg::U_MET_SPHERE:
+      k_pool_half_sweep<hsg::U_MET_SPHERE><<<g, b, 0, st>>>(D, T, NT, S, J, colour, step, hits, hit0, ts);
+      break;
+    case hsg::U_MET_BALL:
+      k_pool_half_sweep<hsg::U_MET_BALL><<<g, b, 0, st>>>(D, T, NT, S, J, colour, step, hits, hit0, ts);
+      break;
+    case hsg::U_MET_OR_SPHERE:
+      k_pool_half_sweep<hsg::U_MET_OR_SPHERE><<<g, b, 0, st>>>(D, T, NT, S, J, colour, step, hits, hit0, ts);
+      break;
+    case hsg::U_MET_OR_BALL:
+      k_pool_half_sweep<hsg::U_MET_OR_BALL><<<g, b, 0, st>>>(D, T, NT, S, J, colour, step, hits, hit0, ts);
+      break;
+    default: k_pool_half_sweep<hsg::U_HB><<<g, b, 0, st>>>(D, T, NT, S, J, colour, step, hits, hit0, ts); break;
   }
   p->launches += 1;
   return cudaGetLastError();
+}
+
+// Passes over each colour for the schedule's main update: the Metropolis
+// hits split into groups of hits_per_pass (the field is fixed for the
+// whole half-sweep and hit j is keyed by j, so any split gives the same
+// result); one pass otherwise.
+int main_passes(const hsg_pool* p, const hsg_schedule* s) {
+  if (s->kind == HSG_NONE) return 0;
+  if (s->kind == HSG_HEATBATH || p->hits_per_pass <= 0 || p->hits_per_pass >= s->hits) return 1;
+  return (s->hits + p->hits_per_pass - 1) / p->hits_per_pass;
 }
 
 // The launches of one sweep, in the single-lattice order: main update on
@@ -429,13 +453,20 @@ cudaError_t enqueue_sweep(hsg_pool* p, const hsg_schedule* s) {
   cudaError_t e = cudaSuccess;
   if (s->kind != HSG_NONE) {
     const bool ball = s->proposal == HSG_PROP_BALL;
-    const int upd = s->kind == HSG_HEATBATH        ? hsg::U_HB
-                    : s->kind == HSG_METROPOLIS_OR ? (ball ? hsg::U_MET_OR_BALL : hsg::U_MET_OR_SPHERE)
-                                                   : (ball ? hsg::U_MET_BALL : hsg::U_MET_SPHERE);
-    for (uint32_t c = 0; c < 2 && e == cudaSuccess; ++c) e = launch_pool_half(p, upd, c, s->step, s->hits);
+    const bool fused = s->kind == HSG_METROPOLIS_OR;
+    const int met = ball ? hsg::U_MET_BALL : hsg::U_MET_SPHERE;
+    const int upd = s->kind == HSG_HEATBATH ? hsg::U_HB : fused ? (ball ? hsg::U_MET_OR_BALL : hsg::U_MET_OR_SPHERE) : met;
+    const int passes = main_passes(p, s);
+    const int per = (s->hits + passes - 1) / passes;
+    for (uint32_t c = 0; c < 2 && e == cudaSuccess; ++c)
+      for (int k = 0, j0 = 0; k < passes && e == cudaSuccess; ++k, j0 += per) {
+        const int n = std::min(per, s->hits - j0);
+        // the fused reflection follows the colour's last hit only
+        e = launch_pool_half(p, (fused && k + 1 < passes) ? met : upd, c, s->step, n, j0);
+      }
   }
   for (int o = 0; o < s->n_or && e == cudaSuccess; ++o)
-    for (uint32_t c = 0; c < 2 && e == cudaSuccess; ++c) e = launch_pool_half(p, hsg::U_OR, c, s->step, s->hits);
+    for (uint32_t c = 0; c < 2 && e == cudaSuccess; ++c) e = launch_pool_half(p, hsg::U_OR, c, s->step, s->hits, 0);
   if (e != cudaSuccess) return e;
   k_pool_advance<<<cdiv_u((unsigned)p->max_slots, 256), 256, 0, p->stream>>>(p->d_desc, p->max_slots);
   p->launches += 1;
@@ -622,8 +653,9 @@ hsg_status hsg_pool_sweep(hsg_pool* p, const hsg_schedule* sched, int n_sweeps) 
   if (n_sweeps < 0) return pfail(p, HSG_EINVAL, "n_sweeps must be >= 0");
   if (n_sweeps == 0 || p->n_active == 0) return HSG_OK;
   if ((st = sync_tables(p)) != HSG_OK) return st;
-  const hsg_pool::GraphKey key{sched->kind, sched->hits, sched->proposal, sched->n_or, sched->renorm_every,
-                               p->threads, p->tile_sites, p->blocks_per_sm, sched->step};
+  const hsg_pool::GraphKey key{sched->kind,    sched->hits,       sched->proposal,      sched->n_or,
+                               sched->renorm_every, p->threads,   p->tile_sites,        p->blocks_per_sm,
+                               p->hits_per_pass, sched->step};
   cudaError_t e = cudaSuccess;
   // One sweep is captured once per (schedule, launch configuration) and
   // replayed; the legacy default stream cannot be captured, so there the
@@ -646,7 +678,7 @@ hsg_status hsg_pool_sweep(hsg_pool* p, const hsg_schedule* sched, int n_sweeps) 
       p->have_graph = true;
       p->gkey = key;
     }
-    const int per_sweep = (sched->kind != HSG_NONE ? 2 : 0) + 2 * sched->n_or + 1 + (sched->renorm_every > 0);
+    const int per_sweep = 2 * main_passes(p, sched) + 2 * sched->n_or + 1 + (sched->renorm_every > 0);
     for (int k = 0; k < n_sweeps && e == cudaSuccess; ++k) {
       e = cudaGraphLaunch(p->gexec, p->stream);
       p->launches += (uint64_t)per_sweep;
@@ -784,20 +816,23 @@ hsg_status hsg_pool_usage(hsg_pool* p, uint64_t* bytes_used, uint64_t* bytes_bud
   return HSG_OK;
 }
 
-hsg_status hsg_pool_config(hsg_pool* p, int threads, int tile_sites, int blocks_per_sm) {
+hsg_status hsg_pool_config(hsg_pool* p, int threads, int tile_sites, int blocks_per_sm, int hits_per_pass) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
   if ((threads != 64 && threads != 128 && threads != 256) || tile_sites < threads || tile_sites % threads != 0 ||
-      tile_sites > 8192 || blocks_per_sm < 1 || blocks_per_sm > 32)
-    return pfail(p, HSG_EINVAL, "threads in {64,128,256}, tile_sites a multiple of threads <= 8192, blocks_per_sm 1..32");
+      tile_sites > 8192 || blocks_per_sm < 1 || blocks_per_sm > 32 || hits_per_pass < 0 || hits_per_pass > 65535)
+    return pfail(p, HSG_EINVAL,
+                 "threads in {64,128,256}, tile_sites a multiple of threads <= 8192, blocks_per_sm 1..32, "
+                 "hits_per_pass 0..65535");
   if (tile_sites != p->tile_sites) p->dirty = true;
   p->threads = threads;
   p->tile_sites = tile_sites;
   p->blocks_per_sm = blocks_per_sm;
+  p->hits_per_pass = hits_per_pass;
   return HSG_OK;
 }
 
 hsg_status hsg_pool_autotune(hsg_pool* p, const hsg_schedule* sched, int* threads, int* tile_sites,
-                             int* blocks_per_sm) {
+                             int* blocks_per_sm, int* hits_per_pass) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
   hsg_status st = check_pool_schedule(p, sched);
   if (st != HSG_OK) return st;
@@ -813,43 +848,54 @@ hsg_status hsg_pool_autotune(hsg_pool* p, const hsg_schedule* sched, int* thread
   if (e != cudaSuccess) return pcuda(p, e, "autotune snapshot");
   std::vector<uint64_t> sweeps;
   for (const Slot& s : p->slots) sweeps.push_back(s.sweep);
-  const int old_t = p->threads, old_ts = p->tile_sites, old_b = p->blocks_per_sm;
-  int best_t = old_t, best_ts = old_ts, best_b = old_b;
+  const int old_t = p->threads, old_ts = p->tile_sites, old_b = p->blocks_per_sm, old_h = p->hits_per_pass;
+  int best_t = old_t, best_ts = old_ts, best_b = old_b, best_h = old_h;
   float best_ms = 1e30f;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // One warm-up sweep (it also captures the graph), then two timed ones.
+  auto trial = [&](int t, int ts, int b, int h) {
+    if (hsg_pool_config(p, t, ts, b, h) != HSG_OK) return true;
+    if ((st = hsg_pool_sweep(p, sched, 1)) != HSG_OK) return false;
+    cudaEventRecord(e0, p->stream);
+    if ((st = hsg_pool_sweep(p, sched, 2)) != HSG_OK) return false;
+    cudaEventRecord(e1, p->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_t = t;
+      best_ts = ts;
+      best_b = b;
+      best_h = h;
+    }
+    return true;
+  };
+  // Launch shape with every Metropolis hit in one pass, then, on that
+  // shape, the hits split over passes of 1, 2, 4, ... hits.
   const int cand_t[] = {128, 256};
   const int cand_ts[] = {256, 512, 1024, 2048};
   const int cand_b[] = {4, 8, 16};
+  bool ok = true;
   for (int t : cand_t)
     for (int ts : cand_ts)
-      for (int b : cand_b) {
-        if (hsg_pool_config(p, t, ts, b) != HSG_OK) continue;
-        if ((st = hsg_pool_sweep(p, sched, 1)) != HSG_OK) break;  // warm-up, builds the graph
-        cudaEventRecord(e0, p->stream);
-        if ((st = hsg_pool_sweep(p, sched, 2)) != HSG_OK) break;
-        cudaEventRecord(e1, p->stream);
-        cudaEventSynchronize(e1);
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_t = t;
-          best_ts = ts;
-          best_b = b;
-        }
-      }
+      for (int b : cand_b)
+        if (ok) ok = trial(t, ts, b, 0);
+  const bool multi_hit = sched->kind == HSG_METROPOLIS || sched->kind == HSG_METROPOLIS_OR;
+  const int shape_t = best_t, shape_ts = best_ts, shape_b = best_b;
+  for (int h = 1; ok && multi_hit && h < sched->hits; h *= 2) ok = trial(shape_t, shape_ts, shape_b, h);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   // Restore the lattices and counters; keep the fastest configuration.
   e = cudaMemcpyAsync(p->arena, snap, hi, cudaMemcpyDeviceToDevice, p->stream);
   cudaFreeAsync(snap, p->stream);
   for (size_t i = 0; i < p->slots.size(); ++i) p->slots[i].sweep = sweeps[i];
-  hsg_pool_config(p, best_t, best_ts, best_b);
+  hsg_pool_config(p, best_t, best_ts, best_b, best_h);
   p->dirty = true;
   if (st != HSG_OK) {
-    hsg_pool_config(p, old_t, old_ts, old_b);
+    hsg_pool_config(p, old_t, old_ts, old_b, old_h);
     return st;
   }
   if (e != cudaSuccess) return pcuda(p, e, "autotune restore");
@@ -857,6 +903,7 @@ hsg_status hsg_pool_autotune(hsg_pool* p, const hsg_schedule* sched, int* thread
   if (threads) *threads = best_t;
   if (tile_sites) *tile_sites = best_ts;
   if (blocks_per_sm) *blocks_per_sm = best_b;
+  if (hits_per_pass) *hits_per_pass = best_h;
   return HSG_OK;
 }
 

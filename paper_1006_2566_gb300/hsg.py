@@ -104,8 +104,9 @@ _SIGS = {
     "hsg_pool_get_spins": ([_vp, _i, _vp, _i], _i),
     "hsg_pool_get_sweep": ([_vp, _i, ctypes.POINTER(_u64)], _i),
     "hsg_pool_usage": ([_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_i)], _i),
-    "hsg_pool_config": ([_vp, _i, _i, _i], _i),
-    "hsg_pool_autotune": ([_vp, _sch_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)], _i),
+    "hsg_pool_config": ([_vp, _i, _i, _i, _i], _i),
+    "hsg_pool_autotune": ([_vp, _sch_p, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                           ctypes.POINTER(_i)], _i),
     "hsg_pool_launch_count": ([_vp, ctypes.POINTER(_u64)], _i),
     "hsg_pool_last_error": ([_vp], ctypes.c_char_p),
 }
@@ -482,15 +483,16 @@ def hsg_pool_usage(pool):
     return used.value, budget.value, active.value
 
 
-def hsg_pool_config(pool, threads: int, tile_sites: int, blocks_per_sm: int) -> None:
-    _pcheck(_lib.hsg_pool_config(pool, int(threads), int(tile_sites), int(blocks_per_sm)), pool)
+def hsg_pool_config(pool, threads: int, tile_sites: int, blocks_per_sm: int, hits_per_pass: int = 0) -> None:
+    _pcheck(_lib.hsg_pool_config(pool, int(threads), int(tile_sites), int(blocks_per_sm), int(hits_per_pass)), pool)
 
 
 def hsg_pool_autotune(pool, sched: hsg_schedule):
-    t, ts, b = _i(0), _i(0), _i(0)
-    _pcheck(_lib.hsg_pool_autotune(pool, ctypes.byref(sched), ctypes.byref(t), ctypes.byref(ts), ctypes.byref(b)),
-            pool)
-    return t.value, ts.value, b.value
+    """(threads, tile_sites, blocks_per_sm, hits_per_pass) chosen and set."""
+    t, ts, b, h = _i(0), _i(0), _i(0), _i(0)
+    _pcheck(_lib.hsg_pool_autotune(pool, ctypes.byref(sched), ctypes.byref(t), ctypes.byref(ts), ctypes.byref(b),
+                                   ctypes.byref(h)), pool)
+    return t.value, ts.value, b.value, h.value
 
 
 def hsg_pool_launch_count(pool) -> int:

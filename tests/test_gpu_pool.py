@@ -126,7 +126,7 @@ def test_pool_with_host_couplings(hsg):
 def test_pool_results_do_not_depend_on_launch_configuration(hsg):
     kw = base_schedule(hsg, "HB")
     outs = []
-    for cfg in [(64, 64, 2), (256, 2048, 16), (128, 384, 5)]:
+    for cfg in [(64, 64, 2, 0), (256, 2048, 16, 0), (128, 384, 5, 0)]:
         with hsg.Pool(1 << 28, 8, torch.cuda.Stream()) as pool:
             hsg.hsg_pool_config(pool.pool, *cfg)
             slots = [pool.admit(*spec) for spec in SPECS]
@@ -145,7 +145,7 @@ def test_pool_autotune_restores_state_and_keeps_results(hsg):
         pool.sweep(hsg.schedule(**kw), 2)
         before = [pool.spins(s) for s in slots]
         cfg = hsg.hsg_pool_autotune(pool.pool, hsg.schedule(**kw))
-        assert cfg[0] in (128, 256) and cfg[1] % cfg[0] == 0 and cfg[2] >= 1
+        assert cfg[0] in (128, 256) and cfg[1] % cfg[0] == 0 and cfg[2] >= 1 and cfg[3] in (0, 1, 2)
         for s, b in zip(slots, before):
             assert np.array_equal(pool.spins(s), b)
             assert pool.sweep_count(s) == 2
@@ -227,3 +227,29 @@ def test_pool_energies_queued_before_a_retirement_survive_reuse_of_the_memory(hs
             with pytest.raises(hsg.HsgError) as err:
                 bad()
             assert err.value.status == hsg.HSG_EINVAL
+
+
+@pytest.mark.parametrize("kind", ["MET", "METOR"])
+def test_pool_metropolis_hits_split_over_passes_give_the_same_result(hsg, kind):
+    """A colour's k Metropolis hits in passes of h hits (h = 1, 2, k - 1)
+    equal all k in one pass bit for bit, and the lattice swept alone: the
+    field is fixed for the half-sweep and hit j is keyed by j; the fused
+    reflection follows the last hit."""
+    kw = dict(base_schedule(hsg, kind), hits=5)
+    outs = []
+    for h in (0, 1, 2, 4):
+        with hsg.Pool(1 << 28, 8, torch.cuda.Stream()) as pool:
+            hsg.hsg_pool_config(pool.pool, 256, 512, 8, h)
+            slots = [pool.admit(*spec) for spec in SPECS]
+            n0 = hsg.hsg_pool_launch_count(pool.pool)
+            pool.sweep(hsg.schedule(**kw), 3)
+            launches = hsg.hsg_pool_launch_count(pool.pool) - n0
+            outs.append([pool.spins(s) for s in slots])
+        passes = 1 if h == 0 else -(-5 // h)
+        assert launches == 3 * (2 * passes + 2 * kw["n_or"] + 1 + 1)  # + counter advance + renormalisation
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+    for got, spec in zip(outs[0], SPECS):
+        want, _ = run_alone(hsg, spec, kw, 3)
+        assert np.array_equal(got, want)
