@@ -37,8 +37,7 @@ constexpr int G_THREADS = 128;
 // an SM (measured at L = 256: OR 92 us at 32 registers vs 99 us at 36-40);
 // Metropolis, which would spill, keeps its registers.
 template <int U>
-__global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
-    k_half_sweep_global(const SweepArgs a) {
+__global__ void __launch_bounds__(G_THREADS, U == U_OR ? 16 : 1) k_half_sweep_global(const SweepArgs a) {
   const uint32_t xh = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t y = blockIdx.y * blockDim.y + threadIdx.y;
   const uint32_t z = blockIdx.z;
