@@ -184,11 +184,38 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def _code_only(text: str) -> str:
+    """C/CUDA source without its comments and with runs of white space
+    folded to one blank: what the compiler sees of it."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":  # a string or character literal, kept whole
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return re.sub(r"\s+", " ", "".join(out)).strip()
+
+
 def kernel_source_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the single-lattice kernels' code
+    (comments and spacing removed), which an ncu summary records to say
+    which kernels its counters belong to."""
     h = hashlib.sha256()
     for f in ("hsg_sweep.cu", "hsg_wave.cu", "hsg_device.cuh"):
-        with open(os.path.join(ROOT, "paper_1006_2566_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1006_2566_gb300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -16,12 +16,14 @@
 //            planes k-1, k, k+1 (a ring of three in shared memory).
 // The bonds and old spins of stage 0 are loaded into registers one step
 // ahead; stage 0 leaves its bonds in shared memory, where stage 1 finds its
-// own (each bond joins a colour-0 and a colour-1 site).  A thread marches up
-// one column, so the neighbours in its own column on three consecutive
-// planes (its -z, one x and its +z neighbour) are read once and carried in
-// registers: four shared-memory reads per site instead of six.  Each spin and bond
+// own (each bond joins a colour-0 and a colour-1 site).  Each spin and bond
 // thus leaves HBM about once per full sweep instead of once per half-sweep:
-// 44 B per site update instead of 72 B.
+// 44 B per site update instead of 72 B.  A thread marches up one column, so
+// the neighbours in its own column on three consecutive planes (its -z, one
+// x and its +z neighbour) are read from shared memory once and carried in
+// registers: four shared-memory reads per site instead of six.  The RENORM
+// instantiation also renormalises every spin it stores, for a
+// renormalisation due right after the sweep.
 //
 // Neighbouring tiles both compute the colour-0 sites of their shared halo;
 // they read the same old values and run the same code (site_result), so the
@@ -32,9 +34,11 @@
 //
 // Shape (measured on GB300 at L = 256): 16 x 14 tiles make R0 exactly nine
 // warps; 51 KB of shared memory per CTA, three CTAs per SM, and the rest of
-// the SM's unified L1/shared array left to L1 (launch_wave).  The
-// heat-bath is not blocked this way: recomputing the halo's Philox draws and
-// transcendentals made it compute-bound and slower than two half-sweeps.
+// the SM's unified L1/shared array left to L1 (launch_wave).  Bringing the
+// colour-1 planes in by TMA instead of per-thread cp.async was slower: one
+// 3-D tensor box per plane 165 us, bulk row copies 231 us, against 155 us.
+// The heat-bath is not blocked this way: recomputing the halo's Philox draws
+// and transcendentals made it compute-bound and slower than two half-sweeps.
 #include "hsg_device.cuh"
 #include "hsg_internal.h"
 
