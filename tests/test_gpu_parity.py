@@ -594,3 +594,45 @@ def test_profiler_counts_launches(hsg):
         assert hsg.hsg_launch_count(lat.ctx) - n0 == 20 + 80 + 10 + 2 * 2 + 2
         hsg.hsg_profile_reset(lat.ctx)
         assert hsg.hsg_profile_read(lat.ctx, hsg.HSG_PROF_OVERRELAX)[1] == 0
+
+
+def test_gpu_matches_the_golden_fixture(hsg):
+    """The CUDA path against the stored oracle results of
+    tests/golden/l6_seed21.json (L = 6, seed 21; the fixture's own fp32
+    couplings and spins): energy, an over-relaxation, a Metropolis (3 hits,
+    ball; every decision of the fixture is >= 5e-4 from its threshold) and a
+    heat-bath half-sweep under the half-sweep rules above, and two sweeps of
+    heat-bath + 1 OR under the whole-sweep rule."""
+    import json
+
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "l6_seed21.json")) as f:
+        g = json.load(f)
+    L, seed = g["L"], g["seed"]
+    J = np.array(g["J"])
+    s0 = np.array(g["s0"]).astype(np.float32)
+    b64 = s0.astype(np.float64)
+    with hsg.Lattice(L, seed) as lat:
+        lat.set_couplings(J.astype(np.float32))
+        lat.set_spins(s0)
+        assert abs(lat.energy() - g["energy_s0"]) <= 2e-6
+    got = gpu_half_sweep(hsg, L, J, s0, hsg.HSG_OVERRELAX, 0, hsg.schedule(), seed=seed, sweep=0)
+    check_half_sweep(L, J, b64, got, np.array(g["or_colour0"]), 0)
+    m = g["met_colour1"]
+    assert min(m["margins"]) >= 1e-5
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=m["hits"], proposal=hsg.HSG_PROP_BALL, step=m["step"], T=m["T"])
+    got = gpu_half_sweep(hsg, L, J, s0, hsg.HSG_METROPOLIS, 1, sched, seed=seed, sweep=m["sweep"])
+    check_half_sweep(L, J, b64, got, np.array(m["spins"]), 1)
+    h = g["hb_colour0"]
+    sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=h["T"])
+    got = gpu_half_sweep(hsg, L, J, s0, hsg.HSG_HEATBATH, 0, sched, seed=seed, sweep=h["sweep"])
+    check_half_sweep(L, J, b64, got, np.array(h["spins"]), 0, exclude=frame_band(L, J, b64, 0))
+    w = g["hb_or_two_sweeps"]
+    with hsg.Lattice(L, seed) as lat:
+        lat.set_couplings(J.astype(np.float32))
+        lat.set_spins(s0)
+        lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, T=w["T"], n_or=w["n_or"], energy_every=1), w["sweeps"])
+        got = lat.spins().astype(np.float64)
+        elog = lat.energy_log()
+    assert np.max(np.abs(elog - np.array(w["energy_log"]))) < 1e-5
+    err = np.max(np.abs(got - np.array(w["spins"])).reshape(-1, 3), axis=1)
+    assert np.median(err) <= TOL

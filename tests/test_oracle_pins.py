@@ -572,3 +572,23 @@ def test_fused_metropolis_over_relaxation_rings_give_langevin_energy(orc):
     _, elog = orc.sweeps(L, J, s, sch, orc.key(3), n)
     mean, err = _binned_mean(elog[n // 5:])
     assert abs(mean + langevin(beta)) < 3 * err + 1e-4, (mean, err)
+
+
+def test_oracle_reproduces_the_golden_fixture(orc):
+    """tests/golden/l6_seed21.json holds the oracle's own results for one
+    L = 6 lattice (written by tests/golden/make_golden.py, which calls only
+    the oracle): the oracle must still produce every stored value exactly,
+    so a change to its arithmetic cannot pass unnoticed (the fixture is then
+    rewritten by that script, deliberately)."""
+    import importlib.util
+    import json
+    import os
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    with open(os.path.join(here, "l6_seed21.json")) as f:
+        want = json.load(f)
+    got = json.loads(json.dumps(mg.compute()))
+    assert got == want
