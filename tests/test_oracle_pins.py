@@ -583,6 +583,7 @@ def test_oracle_reproduces_the_golden_fixture(orc):
     import importlib.util
     import json
     import os
+    import platform
 
     here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
     spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
@@ -591,4 +592,17 @@ def test_oracle_reproduces_the_golden_fixture(orc):
     with open(os.path.join(here, "l6_seed21.json")) as f:
         want = json.load(f)
     got = json.loads(json.dumps(mg.compute()))
-    assert got == want
+    if platform.machine() in ("x86_64", "AMD64"):  # where the fixture was written: bit for bit
+        assert got == want
+        return
+    # another libm may round exp/log/sin/cbrt an ulp differently
+    def numbers(v):
+        if isinstance(v, dict):
+            return [x for key in sorted(v) for x in numbers(v[key])]
+        if isinstance(v, list):
+            return [x for e in v for x in numbers(e)]
+        return [float(v)] if isinstance(v, (int, float)) else []
+
+    assert got.keys() == want.keys() and got["source"] == want["source"]
+    for k in want:
+        assert np.allclose(numbers(got[k]), numbers(want[k]), rtol=0, atol=1e-12), k
