@@ -65,6 +65,10 @@ __global__ void __launch_bounds__(G_THREADS, U == U_OR ? 16 : 1) k_half_sweep_gl
 // 6 planes and 40 registers (12 blocks per SM) 94.0 us, against 100.9 us
 // for one site per thread at 32 registers; 8 planes 95.1, 4 planes 96.0,
 // 16 planes 97.3, 32 planes 107; at 32 registers (spilling) 104-106 us.
+// A persistent grid that deals out equal contiguous (column block, plane)
+// ranges, one CTA per resident slot (no partial last wave), took 105.7 us:
+// neighbouring column blocks then work on different planes, so the rows
+// they share are probably no longer found in L2.
 constexpr int ZM_PLANES = 6;
 
 template <int U>
