@@ -35,7 +35,10 @@ constexpr int G_THREADS = 128;
 // Indices are 32-bit: q < N/2 <= 1624^3/2 < 2^31.  The over-relaxation
 // kernel is held to 32 registers so that 16 blocks (full occupancy) fit on
 // an SM (measured at L = 256: OR 92 us at 32 registers vs 99 us at 36-40);
-// Metropolis, which would spill, keeps its registers.
+// Metropolis, which would spill, keeps its registers.  A grid of exactly
+// the resident CTAs looping over the sites (grid-stride, or an equal
+// contiguous range per CTA; 10 or 12 CTAs per SM) made the 4-hit Metropolis
+// half-sweep at L = 128 slower: 28.1-30.1 us against 25.9 us.
 template <int U>
 __global__ void __launch_bounds__(G_THREADS, U == U_OR ? 16 : 1) k_half_sweep_global(const SweepArgs a) {
   const uint32_t xh = blockIdx.x * blockDim.x + threadIdx.x;
