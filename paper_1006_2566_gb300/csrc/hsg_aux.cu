@@ -356,15 +356,26 @@ cudaError_t launch_add_u64(unsigned long long* p, unsigned long long d, cudaStre
   return cudaGetLastError();
 }
 
-cudaError_t launch_renorm(void* S, bool packed, long long n, int sm_count, cudaStream_t s) {
+// Grid-stride over the spins on the CTAs that are resident at once (one
+// even wave; the float4 kernel holds eight CTAs of 256 per SM, the packed one
+// six).
+template <bool PACKED>
+cudaError_t launch_renorm_layout(void* S, long long n, int sm_count, cudaStream_t s) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_renorm<PACKED>, 256, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+  }
   const long long want = (n + 255) / 256;
-  const long long cap = (long long)sm_count * 8;
+  const long long cap = (long long)(sm_count > 0 ? sm_count : 1) * per_sm;
   const unsigned grid = (unsigned)(want < cap ? want : cap);
-  if (packed)
-    k_renorm<true><<<grid, 256, 0, s>>>(S, n);
-  else
-    k_renorm<false><<<grid, 256, 0, s>>>(S, n);
+  k_renorm<PACKED><<<grid, 256, 0, s>>>(S, n);
   return cudaGetLastError();
+}
+
+cudaError_t launch_renorm(void* S, bool packed, long long n, int sm_count, cudaStream_t s) {
+  return packed ? launch_renorm_layout<true>(S, n, sm_count, s) : launch_renorm_layout<false>(S, n, sm_count, s);
 }
 
 cudaError_t launch_philox(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t n, uint32_t* out,
