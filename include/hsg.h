@@ -23,6 +23,10 @@
  *   - Work is queued on the stream given to hsg_create, in call order.
  *     Functions that return host data synchronise that stream; the others
  *     are asynchronous.
+ *   - A context or pool belongs to the device that was current when it was
+ *     created.  Each call makes that device current for its duration and
+ *     then restores the caller's, so objects of several devices can be used
+ *     from one thread in any order.
  *   - Device memory is owned by the context (stream-ordered allocations),
  *     released by hsg_destroy.  Caller arrays are copied, never retained.
  *   - hsg_last_error() gives a message for the last failure.

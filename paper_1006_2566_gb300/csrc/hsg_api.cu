@@ -173,6 +173,7 @@ hsg_status ensure_stage(hsg_ctx* c, size_t bytes) {
 
 void release(hsg_ctx* c) {
   if (!c) return;
+  const hsg::DeviceGuard device_guard(c->device);
   cudaStream_t s = c->stream;
   dev_free(c->spins, s);
   dev_free(c->spins_alt, s);
@@ -510,6 +511,8 @@ hsg_status hsg_destroy(hsg_ctx* ctx) {
 
 hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!J) return fail(c, HSG_EINVAL, "J is NULL");
   if (dtype != HSG_F32 && dtype != HSG_F64) return fail(c, HSG_EINVAL, "dtype must be HSG_F32 or HSG_F64");
   if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
@@ -537,6 +540,8 @@ hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
 
 hsg_status hsg_generate_couplings(hsg_ctx* c) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   // Key of (seed, sample, replica 0): replicas of one sample share J.
   const uint32_t k1 = (uint32_t)(c->seed >> 32) ^ ((2u * c->sample) * 0x9E3779B9u);
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling generator kernel",
@@ -547,6 +552,8 @@ hsg_status hsg_generate_couplings(hsg_ctx* c) {
 
 hsg_status hsg_get_couplings(hsg_ctx* c, float* out, int where) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!out) return fail(c, HSG_EINVAL, "out is NULL");
   if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
   if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
@@ -570,6 +577,8 @@ hsg_status hsg_get_couplings(hsg_ctx* c, float* out, int where) {
 
 hsg_status hsg_sweep(hsg_ctx* c, const hsg_schedule* s, int n_sweeps) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   hsg_status st = check_schedule(c, s, true);
   if (st != HSG_OK) return st;
   if (n_sweeps < 0) return fail(c, HSG_EINVAL, "n_sweeps must be >= 0");
@@ -621,6 +630,8 @@ hsg_status hsg_sweep(hsg_ctx* c, const hsg_schedule* s, int n_sweeps) {
 
 hsg_status hsg_energy(hsg_ctx* c, double* e_per_spin) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!e_per_spin) return fail(c, HSG_EINVAL, "e_per_spin is NULL");
   if (!c->have_J) return fail(c, HSG_EINVAL, "couplings not set");
   hsg_status st = run_energy(c, c->e_out, false);
@@ -634,6 +645,8 @@ hsg_status hsg_energy(hsg_ctx* c, double* e_per_spin) {
 
 hsg_status hsg_get_energy_log(hsg_ctx* c, double* out, int max_n, int* n) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (max_n < 0 || (max_n > 0 && !out)) return fail(c, HSG_EINVAL, "bad output buffer");
   const int k = max_n < c->elog_n ? max_n : c->elog_n;
   cudaError_t e = cudaSuccess;
@@ -646,6 +659,8 @@ hsg_status hsg_get_energy_log(hsg_ctx* c, double* out, int max_n, int* n) {
 
 hsg_status hsg_clear_energy_log(hsg_ctx* c) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "counter kernel",
                          [&] { return hsg::launch_set_u64(c->d_ctr + 1, 0, c->stream); });
   if (st != HSG_OK) return st;
@@ -655,6 +670,8 @@ hsg_status hsg_clear_energy_log(hsg_ctx* c) {
 
 hsg_status hsg_get_spins(hsg_ctx* c, float* out, int where) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!out) return fail(c, HSG_EINVAL, "out is NULL");
   if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
   const size_t bytes = sizeof(float) * 3 * (size_t)c->N;
@@ -677,6 +694,8 @@ hsg_status hsg_get_spins(hsg_ctx* c, float* out, int where) {
 
 hsg_status hsg_set_spins(hsg_ctx* c, const float* in, int where) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!in) return fail(c, HSG_EINVAL, "in is NULL");
   if (where != HSG_HOST && where != HSG_DEVICE) return fail(c, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
   const float* src = in;
@@ -700,6 +719,8 @@ hsg_status hsg_set_spins(hsg_ctx* c, const float* in, int where) {
 
 hsg_status hsg_get_sites(hsg_ctx* c, const uint32_t* sites, int n, float* spins, float* bonds) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (n < 0) return fail(c, HSG_EINVAL, "n must be >= 0");
   if (n == 0) return HSG_OK;
   if (!sites || !spins) return fail(c, HSG_EINVAL, "sites and spins must not be NULL");
@@ -729,6 +750,8 @@ hsg_status hsg_get_sites(hsg_ctx* c, const uint32_t* sites, int n, float* spins,
 
 hsg_status hsg_get_sweep(hsg_ctx* c, uint64_t* sweep) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!sweep) return fail(c, HSG_EINVAL, "sweep is NULL");
   *sweep = c->sweep;
   return HSG_OK;
@@ -736,6 +759,8 @@ hsg_status hsg_get_sweep(hsg_ctx* c, uint64_t* sweep) {
 
 hsg_status hsg_set_sweep(hsg_ctx* c, uint64_t sweep) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "counter kernel",
                          [&] { return hsg::launch_set_u64(c->d_ctr, sweep, c->stream); });
   if (st != HSG_OK) return st;
@@ -745,6 +770,8 @@ hsg_status hsg_set_sweep(hsg_ctx* c, uint64_t sweep) {
 
 hsg_status hsg_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int colour) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   hsg_status st = check_schedule(c, s, false);
   if (st != HSG_OK) return st;
   if (update != HSG_OVERRELAX && update != HSG_METROPOLIS && update != HSG_HEATBATH && update != HSG_METROPOLIS_OR)
@@ -756,11 +783,15 @@ hsg_status hsg_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int col
 
 hsg_status hsg_renorm(hsg_ctx* c) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   return run_renorm(c);
 }
 
 hsg_status hsg_kernel_for(hsg_ctx* c, const hsg_schedule* s, int* kernel) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!kernel) return fail(c, HSG_EINVAL, "kernel is NULL");
   hsg_status st = check_schedule(c, s, true);
   if (st != HSG_OK) return st;
@@ -770,6 +801,8 @@ hsg_status hsg_kernel_for(hsg_ctx* c, const hsg_schedule* s, int* kernel) {
 
 hsg_status hsg_profile(hsg_ctx* c, int on) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!on) close_run(c);
   c->prof = on != 0;
   return HSG_OK;
@@ -777,6 +810,8 @@ hsg_status hsg_profile(hsg_ctx* c, int on) {
 
 hsg_status hsg_profile_read(hsg_ctx* c, int kclass, double* total_ms, uint64_t* launches) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (kclass < 0 || kclass >= HSG_PROF_COUNT) return fail(c, HSG_EINVAL, "bad kernel class");
   close_run(c);
   cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -798,6 +833,8 @@ hsg_status hsg_profile_read(hsg_ctx* c, int kclass, double* total_ms, uint64_t* 
 
 hsg_status hsg_profile_reset(hsg_ctx* c) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "profile sync");
   close_run(c);
@@ -811,6 +848,8 @@ hsg_status hsg_profile_reset(hsg_ctx* c) {
 
 hsg_status hsg_launch_count(hsg_ctx* c, uint64_t* launches) {
   if (!c) return fail(nullptr, HSG_EINVAL, "ctx is NULL");
+  const hsg::DeviceGuard device_guard(c->device);
+  if (device_guard.status() != cudaSuccess) return cuda_fail(c, device_guard.status(), "cudaSetDevice");
   if (!launches) return fail(c, HSG_EINVAL, "launches is NULL");
   *launches = c->launches;
   return HSG_OK;

@@ -361,11 +361,16 @@ cudaError_t launch_add_u64(unsigned long long* p, unsigned long long d, cudaStre
 // six).
 template <bool PACKED>
 cudaError_t launch_renorm_layout(void* S, long long n, int sm_count, cudaStream_t s) {
-  static int per_sm = 0;
+  static PerDevice resident;  // CTAs of 256 per SM, looked up once per device
+  cudaError_t e = cudaSuccess;
+  std::atomic<int>* slot = device_slot(resident, &e);
+  if (!slot) return e;
+  int per_sm = slot->load(std::memory_order_acquire);
   if (per_sm == 0) {
-    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_renorm<PACKED>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_renorm<PACKED>, 256, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    slot->store(per_sm, std::memory_order_release);
   }
   const long long want = (n + 255) / 256;
   const long long cap = (long long)(sm_count > 0 ? sm_count : 1) * per_sm;

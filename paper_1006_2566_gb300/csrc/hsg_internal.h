@@ -2,6 +2,7 @@
 // kernel translation units.  Not part of the public ABI.
 #pragma once
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -9,6 +10,53 @@
 #include <cuda_runtime.h>
 
 namespace hsg {
+
+// A value kept per device and set once, by whichever host thread gets there
+// first: a kernel attribute applied, an occupancy looked up (0 = not yet).
+// Objects of this type live in static storage, so every slot starts at 0.
+constexpr int kMaxDevices = 64;
+struct PerDevice {
+  std::atomic<int> v[kMaxDevices];
+};
+
+// Makes `dev` the current device for the guard's lifetime and then restores
+// the caller's; no device call beyond cudaGetDevice when it is current
+// already.  Every ABI entry point holds one for its context's or pool's
+// device, so calls on objects of several devices may be mixed freely.
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    err_ = cudaGetDevice(&prev_);
+    if (err_ == cudaSuccess && prev_ != dev) {
+      err_ = cudaSetDevice(dev);
+      switched_ = err_ == cudaSuccess;
+    }
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+  cudaError_t status() const { return err_; }
+
+ private:
+  int prev_ = 0;
+  bool switched_ = false;
+  cudaError_t err_ = cudaSuccess;
+};
+
+// The current device's slot of `pd`; nullptr with *err set when the device
+// cannot be read or its ordinal is beyond kMaxDevices.
+inline std::atomic<int>* device_slot(PerDevice& pd, cudaError_t* err) {
+  int dev = 0;
+  *err = cudaGetDevice(&dev);
+  if (*err != cudaSuccess) return nullptr;
+  if (dev < 0 || dev >= kMaxDevices) {
+    *err = cudaErrorInvalidDevice;
+    return nullptr;
+  }
+  return &pd.v[dev];
+}
 
 // Arguments of one half-sweep (see hsg_device.cuh for the layout).
 struct SweepArgs {

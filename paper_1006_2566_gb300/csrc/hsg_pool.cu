@@ -540,6 +540,7 @@ hsg_status hsg_pool_create(hsg_pool** out, uint64_t budget_bytes, int max_slots,
 
 hsg_status hsg_pool_destroy(hsg_pool* p) {
   if (!p) return HSG_OK;
+  const hsg::DeviceGuard device_guard(p->device);
   if (p->stream || p->arena) cudaStreamSynchronize(p->stream);
   drop_graph(p);
   if (p->stage) cudaFreeAsync(p->stage, p->stream);
@@ -567,6 +568,8 @@ hsg_status hsg_pool_destroy(hsg_pool* p) {
 hsg_status hsg_pool_admit(hsg_pool* p, int L, uint64_t seed, uint32_t sample, uint32_t replica, double T,
                           const void* J, int dtype, int where, int* slot) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (!slot) return pfail(p, HSG_EINVAL, "slot is NULL");
   *slot = -1;
   if (L < 4 || L > 1624 || (L & 1)) return pfail(p, HSG_EINVAL, "L must be even and in [4, 1624]");
@@ -635,6 +638,8 @@ hsg_status hsg_pool_admit(hsg_pool* p, int L, uint64_t seed, uint32_t sample, ui
 
 hsg_status hsg_pool_retire(hsg_pool* p, int slot) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (!valid_slot(p, slot)) return pfail(p, HSG_EINVAL, "no such active slot");
   // No wait: the kernels already queued for this slot run first, and its
   // block is reused only by work queued on the same stream after this call.
@@ -648,6 +653,8 @@ hsg_status hsg_pool_retire(hsg_pool* p, int slot) {
 
 hsg_status hsg_pool_sweep(hsg_pool* p, const hsg_schedule* sched, int n_sweeps) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   hsg_status st = check_pool_schedule(p, sched);
   if (st != HSG_OK) return st;
   if (n_sweeps < 0) return pfail(p, HSG_EINVAL, "n_sweeps must be >= 0");
@@ -752,6 +759,8 @@ hsg_status read_energies(hsg_pool* p, int b, double* out, int n) {
 
 hsg_status hsg_pool_energies(hsg_pool* p, double* out, int n) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (!out || n < 0) return pfail(p, HSG_EINVAL, "bad output buffer");
   const hsg_status st = enqueue_energies(p, 2);
   return st != HSG_OK ? st : read_energies(p, 2, out, n);
@@ -759,12 +768,16 @@ hsg_status hsg_pool_energies(hsg_pool* p, double* out, int n) {
 
 hsg_status hsg_pool_energies_async(hsg_pool* p, int buffer) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
   return enqueue_energies(p, buffer);
 }
 
 hsg_status hsg_pool_energies_slots_async(hsg_pool* p, int buffer, const int* slots, int n) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
   if (n < 0 || (n > 0 && !slots)) return pfail(p, HSG_EINVAL, "bad slot list");
   static const int none = 0;
@@ -773,6 +786,8 @@ hsg_status hsg_pool_energies_slots_async(hsg_pool* p, int buffer, const int* slo
 
 hsg_status hsg_pool_energies_read(hsg_pool* p, int buffer, double* out, int n) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (buffer != 0 && buffer != 1) return pfail(p, HSG_EINVAL, "buffer must be 0 or 1");
   if (!out || n < 0) return pfail(p, HSG_EINVAL, "bad output buffer");
   return read_energies(p, buffer, out, n);
@@ -780,6 +795,8 @@ hsg_status hsg_pool_energies_read(hsg_pool* p, int buffer, double* out, int n) {
 
 hsg_status hsg_pool_get_spins(hsg_pool* p, int slot, float* out, int where) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (!valid_slot(p, slot)) return pfail(p, HSG_EINVAL, "no such active slot");
   if (!out) return pfail(p, HSG_EINVAL, "out is NULL");
   if (where != HSG_HOST && where != HSG_DEVICE) return pfail(p, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
@@ -803,6 +820,8 @@ hsg_status hsg_pool_get_spins(hsg_pool* p, int slot, float* out, int where) {
 
 hsg_status hsg_pool_get_sweep(hsg_pool* p, int slot, uint64_t* sweep) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (!valid_slot(p, slot) || !sweep) return pfail(p, HSG_EINVAL, "no such active slot / NULL");
   *sweep = p->slots[slot].sweep;
   return HSG_OK;
@@ -810,6 +829,8 @@ hsg_status hsg_pool_get_sweep(hsg_pool* p, int slot, uint64_t* sweep) {
 
 hsg_status hsg_pool_usage(hsg_pool* p, uint64_t* bytes_used, uint64_t* bytes_budget, int* active) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if (bytes_used) *bytes_used = p->used;
   if (bytes_budget) *bytes_budget = p->budget;
   if (active) *active = p->n_active;
@@ -818,6 +839,8 @@ hsg_status hsg_pool_usage(hsg_pool* p, uint64_t* bytes_used, uint64_t* bytes_bud
 
 hsg_status hsg_pool_config(hsg_pool* p, int threads, int tile_sites, int blocks_per_sm, int hits_per_pass) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   if ((threads != 64 && threads != 128 && threads != 256) || tile_sites < threads || tile_sites % threads != 0 ||
       tile_sites > 8192 || blocks_per_sm < 1 || blocks_per_sm > 32 || hits_per_pass < 0 || hits_per_pass > 65535)
     return pfail(p, HSG_EINVAL,
@@ -834,6 +857,8 @@ hsg_status hsg_pool_config(hsg_pool* p, int threads, int tile_sites, int blocks_
 hsg_status hsg_pool_autotune(hsg_pool* p, const hsg_schedule* sched, int* threads, int* tile_sites,
                              int* blocks_per_sm, int* hits_per_pass) {
   if (!p) return pfail(nullptr, HSG_EINVAL, "pool is NULL");
+  const hsg::DeviceGuard device_guard(p->device);
+  if (device_guard.status() != cudaSuccess) return pcuda(p, device_guard.status(), "cudaSetDevice");
   hsg_status st = check_pool_schedule(p, sched);
   if (st != HSG_OK) return st;
   if (p->n_active == 0) return pfail(p, HSG_EINVAL, "autotune needs admitted lattices");

@@ -325,17 +325,20 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
 constexpr int W_CARVEOUT_PCT = 58;
 constexpr int W_GRID_PER_SM = 3;
 
+// The kernel attributes are per device: applied once on each device used.
 template <bool RENORM>
 cudaError_t configure_wave() {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM);
+  static PerDevice configured;
+  cudaError_t e = cudaSuccess;
+  std::atomic<int>* slot = device_slot(configured, &e);
+  if (!slot) return e;
+  if (slot->load(std::memory_order_acquire) == 0) {
+    e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                W_CARVEOUT_PCT);
     if (e != cudaSuccess) return e;
-    configured = true;
+    slot->store(1, std::memory_order_release);
   }
   return cudaSuccess;
 }
