@@ -88,7 +88,7 @@ PAPER_CONTEXT = {
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serving"], default="l256_hb_or")
@@ -123,6 +123,9 @@ class ClockSampler:
         self.enabled = enabled
 
     def start(self):
+        """Start sampling every 100 ms and wait (at most 3 s) for the first
+        sample, so that the timed region that follows is sampled from its
+        start."""
         if not self.enabled:
             return
         try:
@@ -134,12 +137,18 @@ class ClockSampler:
             return
         self._t = threading.Thread(target=self._read, daemon=True)
         self._t.start()
+        deadline = time.time() + 3.0
+        while not self.lines and time.time() < deadline:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, window=None):
+        """Stop sampling; summarise the samples that arrived within `window`
+        (wall-clock start, end of the timed region; one sampling interval of
+        grace at the end), or all of them when none did."""
         if self.proc is None:
             return None
         time.sleep(0.15)
@@ -149,9 +158,13 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self._t.join(timeout=2)
+        lines = self.lines
+        in_window = window is not None and any(window[0] <= t <= window[1] + 0.1 for t, _ in lines)
+        if in_window:
+            lines = [(t, ln) for t, ln in lines if window[0] <= t <= window[1] + 0.1]
         sm, smax, power, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for _, ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -167,7 +180,8 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "reasons": sorted(reasons),
+                "window": "timed region" if in_window else "whole run (no sample fell in the timed region)"}
 
 
 # ---------------------------------------------------------------------------
@@ -334,24 +348,26 @@ def run_ours(args, wl):
     for _ in range(args.warmup):
         lat.sweep(sched, sps)
     torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device(), enabled=not args.no_clocks and rank == 0)
+    clocks.start()
     if world > 1:
         torch.distributed.barrier()
     # Timed region: K steps as a user runs them (sweep periods replayed as
     # CUDA graphs), CUDA events on the library's stream.
-    clocks = ClockSampler(torch.cuda.current_device(), enabled=not args.no_clocks and rank == 0)
-    clocks.start()
     n_launch0 = hsg.hsg_launch_count(lat.ctx)
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
+    wall0 = time.time()
     t0.record(stream)
     for _ in range(args.steps):
         lat.sweep(sched, sps)
     t1.record(stream)
     torch.cuda.synchronize()
+    wall1 = time.time()
     if world > 1:
         torch.distributed.barrier()
-    clk = clocks.stop()
+    clk = clocks.stop((wall0, wall1))
     elapsed_ms = t0.elapsed_time(t1)
     launches = hsg.hsg_launch_count(lat.ctx) - n_launch0
     # The same K steps again with the library's profiler on: every kernel is
