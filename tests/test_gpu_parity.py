@@ -295,6 +295,42 @@ def test_heatbath_half_sweep_parity(hsg, variant, L, T):
         assert np.max(np.abs(np.linalg.norm(got.reshape(-1, 3)[mask], axis=1) - 1)) < 1e-5
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_zero_field_half_sweeps(hsg, variant):
+    """All couplings zero, so h = 0 at every site at a finite temperature
+    (the degenerate case of the field): over-relaxation leaves every spin
+    as it is, bit for bit; the heat-bath draws uniformly on the sphere
+    (1/|h| is infinite there, not beta = 0); Metropolis accepts every
+    proposal (dE = 0).  Heat-bath and Metropolis against the oracle."""
+    L = 8
+    J = np.zeros(3 * L ** 3)
+    s32 = inputs.random_spins(L, seed=77, dtype=np.float32)
+    s64 = s32.astype(np.float64)
+    for colour in (0, 1):
+        mask = colour_mask(L, colour)
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_OVERRELAX, colour, hsg.schedule(kernel=variant))
+        assert np.array_equal(got, s64)
+
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_HEATBATH, colour,
+                             hsg.schedule(kind=hsg.HSG_HEATBATH, T=0.5, kernel=variant), seed=19, sweep=2)
+        ref = s64.copy()
+        oracle.half_sweep(L, J, ref, oracle.HB, colour, oracle.Params(key=oracle.key(19), sweep=2, beta=2.0))
+        assert np.max(np.abs(got - ref)) <= TOL
+        assert np.all(np.any(got.reshape(-1, 3)[mask] != s64.reshape(-1, 3)[mask], axis=1))
+
+        sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=2, proposal=hsg.HSG_PROP_BALL, step=0.5, T=0.5,
+                             kernel=variant)
+        got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_METROPOLIS, colour, sched, seed=19, sweep=2)
+        ref = s64.copy()
+        p = oracle.Params(key=oracle.key(19), sweep=2, beta=2.0, step=0.5, hits=2, proposal=oracle.PROP_BALL)
+        margins = oracle.half_sweep(L, J, ref, oracle.MET, colour, p, want_margins=True)
+        near = mask & (margins < TOL)
+        assert near.sum() <= 2
+        err = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
+        assert np.all(err[mask & ~near] <= TOL)
+        assert np.all(np.any(ref.reshape(-1, 3)[mask] != s64.reshape(-1, 3)[mask], axis=1))  # every site moved
+
+
 @pytest.mark.parametrize("L", [4, 8, 14, 40, 66])  # the heat-bath column march: shorter than, and ragged in, its 6-plane chunks
 def test_kernel_variants_are_bit_identical(hsg, L):
     J = inputs.gaussian_couplings(L, seed=3)
