@@ -204,6 +204,7 @@ MET_CASES = [
     (40, 1, 4, 0.5),
     (66, 0, 3, 0.3),
     (24, 1, 2, math.inf),
+    (16, 1, 4, 0.01),  # beta = 100: exp(-beta dE) underflows for most uphill proposals
 ]
 
 
@@ -276,7 +277,7 @@ def test_fused_long_run_energy_statistics_match_oracle(hsg):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("L,T", [(6, 1.0), (16, 0.3), (40, 0.3), (66, 1.0), (16, math.inf)])
+@pytest.mark.parametrize("L,T", [(6, 1.0), (16, 0.3), (40, 0.3), (66, 1.0), (16, math.inf), (16, 0.01)])
 def test_heatbath_half_sweep_parity(hsg, variant, L, T):
     J, s32 = oracle_state(L, 500 + L, 600 + L)
     Jr = inputs.round_to_f32(J)
