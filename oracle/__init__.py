@@ -69,9 +69,11 @@ _u32p = ctypes.POINTER(ctypes.c_uint32)
 
 
 def _load():
+    """The compiled oracle; HSG_ORACLE_LIB names another build of the same
+    source to load instead (the mutation tests plant mistakes in copies)."""
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build())
+        lib = ctypes.CDLL(os.environ.get("HSG_ORACLE_LIB") or build())
         lib.oracle_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         lib.oracle_key.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _u32p]
         lib.oracle_counter.argtypes = [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int, ctypes.c_int,
