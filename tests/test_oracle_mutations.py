@@ -52,6 +52,11 @@ MUTATIONS = [
     ("renormalisation by |s|^2", "double nrm = sqrt(dot3(&s[3 * i], &s[3 * i]));",
      "double nrm = dot3(&s[3 * i], &s[3 * i]);"),
     ("Box-Muller: J_z from u1", "out[2] = b * cos(2.0 * ORACLE_PI * u3);", "out[2] = b * cos(2.0 * ORACLE_PI * u1);"),
+    ("key: sample and replica transposed", "(2u * sample + replica)", "(2u * replica + sample)"),
+    ("counter: colour and hit fields swapped", "((uint32_t)colour << 16) | (uint32_t)hit;",
+     "((uint32_t)hit << 16) | (uint32_t)colour;"),
+    ("fused pass: the old spin reflected", "update_or(mid, h, out);", "update_or(s, h, out);"),
+    ("heat-bath: cos(theta) = s - 1", "double ct = 1.0 - sv;", "double ct = sv - 1.0;"),
 ]
 
 
