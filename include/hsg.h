@@ -158,10 +158,14 @@ typedef struct hsg_ctx hsg_ctx; /* opaque, library-owned */
  * Spins start uniform on S^2, drawn from Philox kind 1 at counter site i,
  * sweep 0 (Sec. 2: unit 3-vector spins).  The sweep counter starts at 0.
  * L must be even (the checkerboard needs it under periodic wrap) and in
- * [4, 1624] (site indices fit 32 bits).  Couplings must be set with
- * hsg_set_couplings before any sweep.
- * Errors: HSG_EINVAL (out == NULL, bad L), HSG_ENOMEM, HSG_ECUDA (no
- * device); *out is NULL on error and nothing leaks.
+ * [4, 1624] (site indices fit 32 bits).  replica must be 0 or 1 and
+ * sample < 2^31: the key's stream number 2*sample + replica (see
+ * hsg_schedule) names each pair once only in that range, and two pairs
+ * sharing a key would share every random number.  Couplings must be set
+ * with hsg_set_couplings before any sweep.
+ * Errors: HSG_EINVAL (out == NULL, bad L, replica > 1, sample >= 2^31),
+ * HSG_ENOMEM, HSG_ECUDA (no device); *out is NULL on error and nothing
+ * leaks.
  */
 hsg_status hsg_create(hsg_ctx** out, int L, uint64_t seed, uint32_t sample, uint32_t replica,
                       void* cuda_stream);
@@ -306,7 +310,8 @@ int hsg_version(void);
  * replica)).  out: device array of 4*n uint32, queued on `cuda_stream`.
  * The same device function feeds every update kernel; this entry point
  * exposes it so that its words can be compared with other Philox
- * implementations.  Errors: HSG_EINVAL (out NULL), HSG_ECUDA.
+ * implementations.  Errors: HSG_EINVAL (out NULL or not 16-byte aligned,
+ * replica > 1, sample >= 2^31, as for hsg_create), HSG_ECUDA.
  */
 hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t c1, uint32_t c2, uint32_t c3,
                       uint32_t n, uint32_t* out, void* cuda_stream);
@@ -332,8 +337,9 @@ hsg_status hsg_pool_create(hsg_pool** out, uint64_t budget_bytes, int max_slots,
 hsg_status hsg_pool_destroy(hsg_pool* pool); /* NULL ok; waits for the stream */
 
 /* Admit one lattice: side L (even, 4..1624), Philox key from (seed,
- * sample, replica), temperature T (> 0, inf allowed); spins start as in
- * hsg_create; couplings from J (site-major, dtype / where as in
+ * sample, replica) with replica 0 or 1 and sample < 2^31 (HSG_EINVAL
+ * otherwise, as for hsg_create), temperature T (> 0, inf allowed); spins
+ * start as in hsg_create; couplings from J (site-major, dtype / where as in
  * hsg_set_couplings) or, with J == NULL, generated on the device as by
  * hsg_generate_couplings.  *slot receives the lattice's slot index, its
  * sweep counter starts at 0.  HSG_EBUSY (nothing changed) when no slot is
@@ -419,18 +425,25 @@ hsg_status hsg_test_fail_alloc(int k);
  *
  * spins: device, site-major fp32 s[3*N]; J: device, site-major fp32 J[3*N]
  * (layouts at the top of this file); e_out: device, one double, receives
- * E/N (Eq. 1, each bond once; per-site terms fp32, sums fp64).  Queued on
- * `cuda_stream` (NULL = legacy default stream); nothing is synchronised.
- * L must be even and in [4, 1624]; larger or odd L is rejected with
- * HSG_EINVAL and a message in hsg_last_error(NULL).
+ * E/N, where E = - sum over the 3N nearest-neighbour bonds of J times the
+ * dot product of the two spins it joins, each bond counted once (per-site
+ * terms fp32, sums fp64).  Queued on `cuda_stream` (NULL = legacy default
+ * stream); nothing is synchronised.  L must be even and in [4, 1624];
+ * larger or odd L is rejected with HSG_EINVAL and a message in
+ * hsg_last_error(NULL).  Each of spins, J and e_out must be device memory
+ * of the current device (or managed memory), else HSG_EINVAL before any
+ * launch; the arrays' lengths cannot be checked here and are the caller's
+ * to get right.
  *
  * Scratch: the per-block partial sums live in a fixed device array of
  * HSG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
  * the process exits.  The first call on a device (with that device current)
  * looks up the array's device address and caches it; make that first call
- * before any stream capture.  All calls share the array: calls whose
- * kernels overlap on the GPU (e.g. on two streams) race and must be ordered
- * by the caller.  Errors: HSG_EINVAL, HSG_ECUDA.
+ * before any stream capture.  The cached address does not survive
+ * cudaDeviceReset: do not call this entry point on a device after resetting
+ * it.  All calls share the array: calls whose kernels overlap on the GPU
+ * (e.g. on two streams) race and must be ordered by the caller.
+ * Errors: HSG_EINVAL, HSG_ECUDA.
  */
 #define HSG_NOALLOC_SCRATCH_BYTES 8192
 hsg_status hsg_energy_noalloc(int L, const float* spins, const float* J, double* e_out, void* cuda_stream);

@@ -167,10 +167,16 @@ def philox4x32_10(ctr, key) -> np.ndarray:
     return np.array(list(o), dtype=np.uint32)
 
 
+def _stream_ok(rc: int, sample: int, replica: int) -> None:
+    if rc != 0:
+        raise ValueError(f"(sample {sample}, replica {replica}) outside the key's range: replica must be 0 or 1 "
+                         "and sample < 2**31 (the stream number 2*sample + replica must name each pair once)")
+
+
 def key(seed: int, sample: int = 0, replica: int = 0) -> tuple:
     lib = _load()
     k = (ctypes.c_uint32 * 2)()
-    lib.oracle_key(int(seed), int(sample), int(replica), k)
+    _stream_ok(lib.oracle_key(int(seed), int(sample), int(replica), k), sample, replica)
     return (int(k[0]), int(k[1]))
 
 
@@ -191,14 +197,14 @@ def colour(L: int, i: int) -> int:
 
 def init_spins(L: int, seed: int, sample: int = 0, replica: int = 0) -> np.ndarray:
     s = np.zeros(3 * L ** 3, dtype=np.float64)
-    _load().oracle_init_spins(int(L), int(seed), int(sample), int(replica), _d(s))
+    _stream_ok(_load().oracle_init_spins(int(L), int(seed), int(sample), int(replica), _d(s)), sample, replica)
     return s
 
 
 def gaussian_couplings(L: int, seed: int, sample: int = 0) -> np.ndarray:
     """J ~ N(0,1) from Philox (kind JGEN) and Box-Muller, site-major."""
     J = np.zeros(3 * L ** 3, dtype=np.float64)
-    _load().oracle_gaussian_couplings(int(L), int(seed), int(sample), _d(J))
+    _stream_ok(_load().oracle_gaussian_couplings(int(L), int(seed), int(sample), _d(J)), sample, 0)
     return J
 
 
@@ -206,8 +212,9 @@ def init_spin_sites(sites, seed: int, sample: int = 0, replica: int = 0) -> np.n
     """Initial spins (n, 3) of listed site-major indices (any lattice size)."""
     idx = np.ascontiguousarray(np.asarray(sites, dtype=np.uint32).reshape(-1))
     out = np.zeros(3 * idx.size, dtype=np.float64)
-    _load().oracle_init_spin_sites(int(seed), int(sample), int(replica),
-                                   idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), idx.size, _d(out))
+    rc = _load().oracle_init_spin_sites(int(seed), int(sample), int(replica),
+                                        idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), idx.size, _d(out))
+    _stream_ok(rc, sample, replica)
     return out.reshape(-1, 3)
 
 
@@ -215,8 +222,9 @@ def gaussian_coupling_sites(sites, seed: int, sample: int = 0) -> np.ndarray:
     """+x/+y/+z couplings (n, 3) of listed site-major indices (any lattice size)."""
     idx = np.ascontiguousarray(np.asarray(sites, dtype=np.uint32).reshape(-1))
     out = np.zeros(3 * idx.size, dtype=np.float64)
-    _load().oracle_gaussian_coupling_sites(int(seed), int(sample), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)),
-                                           idx.size, _d(out))
+    rc = _load().oracle_gaussian_coupling_sites(int(seed), int(sample),
+                                                idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), idx.size, _d(out))
+    _stream_ok(rc, sample, 0)
     return out.reshape(-1, 3)
 
 

@@ -109,11 +109,17 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
 }
 
 /* Key of one (seed, sample, replica): k0 = low word of the seed, k1 = high
- * word XOR (2*sample + replica) * 0x9E3779B9 (mod 2^32). */
-void oracle_key(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t key[2]) {
+ * word XOR (2*sample + replica) * 0x9E3779B9 (mod 2^32).  The stream number
+ * 2*sample + replica names each (sample, replica) once only while
+ * replica < 2 and sample < 2^31 (beyond, two pairs would share a key and
+ * every random number): returns -1 and writes nothing outside that range,
+ * else 0. */
+int oracle_key(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t key[2]) {
+  if (replica > 1u || sample >= 0x80000000u) return -1;
   uint32_t stream = (uint32_t)(2u * sample + replica) * 0x9E3779B9u;
   key[0] = (uint32_t)(seed & 0xFFFFFFFFu);
   key[1] = (uint32_t)(seed >> 32) ^ stream;
+  return 0;
 }
 
 /* Counter of one draw: (site, sweep low word, kind<<24 | colour<<16 | hit,
@@ -179,19 +185,21 @@ static void init_spin_at(const uint32_t key[2], uint32_t i, double out[3]) {
   sphere_point(oracle_u01(r[0]), oracle_u01(r[1]), out);
 }
 
-void oracle_init_spins(int L, uint64_t seed, uint32_t sample, uint32_t replica, double* s) {
+int oracle_init_spins(int L, uint64_t seed, uint32_t sample, uint32_t replica, double* s) {
   uint32_t key[2];
   int64_t n = (int64_t)L * L * L;
-  oracle_key(seed, sample, replica, key);
+  if (oracle_key(seed, sample, replica, key) != 0) return -1;
   for (int64_t i = 0; i < n; ++i) init_spin_at(key, (uint32_t)i, &s[3 * i]);
+  return 0;
 }
 
 /* The same for n listed sites (any lattice size): out[3k..3k+2] = spin of sites[k]. */
-void oracle_init_spin_sites(uint64_t seed, uint32_t sample, uint32_t replica, const uint32_t* sites, int n,
-                            double* out) {
+int oracle_init_spin_sites(uint64_t seed, uint32_t sample, uint32_t replica, const uint32_t* sites, int n,
+                           double* out) {
   uint32_t key[2];
-  oracle_key(seed, sample, replica, key);
+  if (oracle_key(seed, sample, replica, key) != 0) return -1;
   for (int k = 0; k < n; ++k) init_spin_at(key, sites[k], &out[3 * k]);
+  return 0;
 }
 
 /* Gaussian couplings J ~ N(0,1) (Sec. 2: Gaussian, mean 0, variance 1),
@@ -214,18 +222,20 @@ static void couplings_at(const uint32_t key[2], uint32_t i, double out[3]) {
   out[2] = b * cos(2.0 * ORACLE_PI * u3);
 }
 
-void oracle_gaussian_couplings(int L, uint64_t seed, uint32_t sample, double* J) {
+int oracle_gaussian_couplings(int L, uint64_t seed, uint32_t sample, double* J) {
   uint32_t key[2];
   int64_t n = (int64_t)L * L * L;
-  oracle_key(seed, sample, 0, key);
+  if (oracle_key(seed, sample, 0, key) != 0) return -1;
   for (int64_t i = 0; i < n; ++i) couplings_at(key, (uint32_t)i, &J[3 * i]);
+  return 0;
 }
 
 /* The same for n listed sites: out[3k + d] = J of the bond from sites[k] to +e_d. */
-void oracle_gaussian_coupling_sites(uint64_t seed, uint32_t sample, const uint32_t* sites, int n, double* out) {
+int oracle_gaussian_coupling_sites(uint64_t seed, uint32_t sample, const uint32_t* sites, int n, double* out) {
   uint32_t key[2];
-  oracle_key(seed, sample, 0, key);
+  if (oracle_key(seed, sample, 0, key) != 0) return -1;
   for (int k = 0; k < n; ++k) couplings_at(key, sites[k], &out[3 * k]);
+  return 0;
 }
 
 /* Local field of site i (Eq. 2 with reading R2):

@@ -435,6 +435,7 @@ hsg_status hsg_create_layout(hsg_ctx** out, int L, uint64_t seed, uint32_t sampl
     return fail(nullptr, HSG_EINVAL, "L must be even and in [4, " + std::to_string(kMaxL) + "]");
   if (layout != HSG_LAYOUT_FLOAT4 && layout != HSG_LAYOUT_PACKED)
     return fail(nullptr, HSG_EINVAL, "layout must be HSG_LAYOUT_FLOAT4 or HSG_LAYOUT_PACKED");
+  if (!hsg::key_stream_ok(sample, replica)) return fail(nullptr, HSG_EINVAL, hsg::kKeyStreamMsg);
   hsg_ctx* c = new (std::nothrow) hsg_ctx();
   if (!c) return fail(nullptr, HSG_ENOMEM, "host allocation failed");
   c->packed = layout == HSG_LAYOUT_PACKED;
@@ -875,6 +876,7 @@ hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t
                       uint32_t n, uint32_t* out, void* cuda_stream) {
   if (!out) return fail(nullptr, HSG_EINVAL, "out is NULL");
   if (reinterpret_cast<uintptr_t>(out) % 16 != 0) return fail(nullptr, HSG_EINVAL, "out must be 16-byte aligned");
+  if (!hsg::key_stream_ok(sample, replica)) return fail(nullptr, HSG_EINVAL, hsg::kKeyStreamMsg);
   const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu);
   const uint32_t k1 = (uint32_t)(seed >> 32) ^ ((2u * sample + replica) * 0x9E3779B9u);
   cudaError_t e = hsg::launch_philox(k0, k1, c1, c2, c3, n, out, static_cast<cudaStream_t>(cuda_stream));

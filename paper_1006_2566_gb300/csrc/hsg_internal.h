@@ -58,6 +58,13 @@ inline std::atomic<int>* device_slot(PerDevice& pd, cudaError_t* err) {
   return &pd.v[dev];
 }
 
+// The Philox key's stream number 2*sample + replica names each (sample,
+// replica) pair once only for replica < 2 and sample < 2^31; beyond, two
+// pairs would share a key and every random number.
+inline bool key_stream_ok(uint32_t sample, uint32_t replica) { return replica <= 1u && sample < 0x80000000u; }
+constexpr const char* kKeyStreamMsg = "replica must be 0 or 1 and sample < 2^31 (the Philox key's stream number "
+                                      "2*sample + replica must name each pair once)";
+
 // Arguments of one half-sweep (see hsg_device.cuh for the layout).
 struct SweepArgs {
   float4* own;          // spins of the colour being updated

@@ -14,7 +14,10 @@
 // The scratch array is shared by every call on a device and keeps the last
 // call's contents; each call overwrites exactly the slots it later reads, so
 // nothing needs clearing.  Two calls whose kernels overlap on the GPU (for
-// example on two streams) race on the array; callers must order them.
+// example on two streams) race on the array; callers must order them.  The
+// array's device address is looked up once per device and cached; a
+// cudaDeviceReset ends the context that address belongs to, so the cache
+// does not survive it.
 #include <mutex>
 #include <string>
 
@@ -101,6 +104,26 @@ hsg_status noalloc_fail(hsg_status st, const std::string& msg) {
   return st;
 }
 
+// HSG_OK when `p` is device memory of device `dev` or managed memory, else
+// HSG_EINVAL (a host pointer would make the kernels fault).  Allocates
+// nothing.
+hsg_status check_device_pointer(const void* p, int dev, const char* name) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // an unknown pointer must not stick to the next call
+    return noalloc_fail(HSG_EINVAL, std::string("hsg_energy_noalloc: ") + name + " is not a device pointer (" +
+                                        cudaGetErrorString(e) + ")");
+  }
+  if (a.type == cudaMemoryTypeManaged) return HSG_OK;
+  if (a.type != cudaMemoryTypeDevice)
+    return noalloc_fail(HSG_EINVAL, std::string("hsg_energy_noalloc: ") + name + " is not device memory");
+  if (a.device != dev)
+    return noalloc_fail(HSG_EINVAL, std::string("hsg_energy_noalloc: ") + name + " belongs to device " +
+                                        std::to_string(a.device) + ", not the current device " + std::to_string(dev));
+  return HSG_OK;
+}
+
 }  // namespace
 
 extern "C" hsg_status hsg_energy_noalloc(int L, const float* spins, const float* J, double* e_out,
@@ -115,6 +138,14 @@ extern "C" hsg_status hsg_energy_noalloc(int L, const float* spins, const float*
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(HSG_ECUDA, std::string("hsg_energy_noalloc: ") + cudaGetErrorString(e));
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(HSG_EINVAL, "hsg_energy_noalloc: device ordinal too large");
+  const struct {
+    const void* p;
+    const char* name;
+  } args[] = {{spins, "spins"}, {J, "J"}, {e_out, "e_out"}};
+  for (const auto& a : args) {
+    const hsg_status st = check_device_pointer(a.p, dev, a.name);
+    if (st != HSG_OK) return st;
+  }
   void* scratch = nullptr;
   {
     // First call on this device: look up the device address of the scratch

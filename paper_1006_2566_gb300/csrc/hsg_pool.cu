@@ -574,6 +574,7 @@ hsg_status hsg_pool_admit(hsg_pool* p, int L, uint64_t seed, uint32_t sample, ui
   *slot = -1;
   if (L < 4 || L > 1624 || (L & 1)) return pfail(p, HSG_EINVAL, "L must be even and in [4, 1624]");
   if (!(T > 0.0)) return pfail(p, HSG_EINVAL, "T must be > 0 (inf allowed)");
+  if (!hsg::key_stream_ok(sample, replica)) return pfail(p, HSG_EINVAL, hsg::kKeyStreamMsg);
   if (J && dtype != HSG_F32 && dtype != HSG_F64) return pfail(p, HSG_EINVAL, "dtype must be HSG_F32 or HSG_F64");
   if (J && where != HSG_HOST && where != HSG_DEVICE) return pfail(p, HSG_EINVAL, "where must be HSG_HOST or HSG_DEVICE");
   int idx = -1;

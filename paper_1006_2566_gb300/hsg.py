@@ -316,14 +316,31 @@ def hsg_test_fail_alloc(k: int) -> None:
 def hsg_energy_noalloc(L: int, spins, J, e_out, stream=None) -> None:
     """E/N of caller-held device arrays (site-major fp32 spins and J) into the
     device double ``e_out``, queued on ``stream``; the library allocates
-    nothing (see include/hsg.h for who needs this)."""
+    nothing (see include/hsg.h for who needs this).
+
+    The library cannot see the arrays' lengths, so they are checked here:
+    float32 ``spins`` and ``J`` of at least 3 L^3 elements and a float64
+    ``e_out`` of at least one, all CUDA tensors on the current device
+    (ValueError otherwise).  An L outside [4, 1624] or odd goes to the
+    library, which rejects it with HSG_EINVAL before launching anything."""
+    import torch
+
+    L = int(L)
+    dev = torch.cuda.current_device()
+    want = [("spins", spins, HSG_F32, 3 * L ** 3), ("J", J, HSG_F32, 3 * L ** 3), ("e_out", e_out, HSG_F64, 1)]
     ptrs = []
-    for a in (spins, J, e_out):
-        ptr, where, _, _ = _array_ptr(a)
-        if where != HSG_DEVICE:
-            raise ValueError("hsg_energy_noalloc takes CUDA tensors")
+    for name, a, code_want, n_want in want:
+        if not isinstance(a, torch.Tensor) or not a.is_cuda:
+            raise ValueError(f"hsg_energy_noalloc: {name} must be a CUDA tensor")
+        if a.device.index != dev:
+            raise ValueError(f"hsg_energy_noalloc: {name} is on {a.device}, not the current device cuda:{dev}")
+        ptr, _, code, n = _array_ptr(a)
+        if code != code_want:
+            raise ValueError(f"hsg_energy_noalloc: {name} must be {'float32' if code_want == HSG_F32 else 'float64'}")
+        if L % 2 == 0 and 4 <= L <= 1624 and n < n_want:  # any other L: the library's HSG_EINVAL, no launch
+            raise ValueError(f"hsg_energy_noalloc: {name} holds {n} elements, needs {n_want} for L = {L}")
         ptrs.append(ptr)
-    _check(_lib.hsg_energy_noalloc(int(L), ptrs[0], ptrs[1], ptrs[2], _stream_ptr(stream)))
+    _check(_lib.hsg_energy_noalloc(L, ptrs[0], ptrs[1], ptrs[2], _stream_ptr(stream)))
 
 
 # ---------------------------------------------------------------------------

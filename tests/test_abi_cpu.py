@@ -64,6 +64,16 @@ def test_host_side_argument_checks(lib):
         assert e.value.status == hsg.HSG_EINVAL
         assert "L must be even" in hsg.hsg_last_error(None)
     assert hsg._lib.hsg_create(None, 8, 1, 0, 0, None) == hsg.HSG_EINVAL
+    # the key's stream number 2*sample + replica must name each pair once:
+    # (s, 2) would share every random number with (s + 1, 0), and sample
+    # 2^31 + s with sample s
+    for sample, replica in ((0, 2), (5, 3), (2 ** 31, 0), (2 ** 32 - 1, 1)):
+        with pytest.raises(hsg.HsgError) as e:
+            hsg.hsg_create(8, seed=1, sample=sample, replica=replica)
+        assert e.value.status == hsg.HSG_EINVAL
+        assert "replica must be 0 or 1" in hsg.hsg_last_error(None)
+        out = ctypes.c_void_p(16)  # aligned, never written: the check comes first
+        assert hsg._lib.hsg_philox(1, sample, replica, 0, 0, 0, 4, out, None) == hsg.HSG_EINVAL
     assert hsg._lib.hsg_test_fail_alloc(-1) == hsg.HSG_EINVAL
     assert hsg._lib.hsg_test_fail_alloc(0) == hsg.HSG_OK
     # NULL / misaligned outputs are refused before any launch

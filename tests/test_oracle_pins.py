@@ -107,6 +107,27 @@ def test_key_and_counter_layout(orc):
     assert c == (12345, 77, (4 << 24) | (1 << 16) | 3, 9)
 
 
+def test_key_names_each_sample_and_replica_once(orc):
+    """Within replica in {0, 1} and sample < 2^31 the stream number
+    2*sample + replica is one-to-one, so distinct pairs have distinct keys;
+    outside that range two pairs would share a key (e.g. (s, 2) and (s+1, 0))
+    and every random number, so the oracle refuses them."""
+    keys = {orc.key(9, s, r) for s in list(range(64)) + [2 ** 31 - 1] for r in (0, 1)}
+    assert len(keys) == 2 * 65
+    for sample, replica in ((0, 2), (5, 3), (2 ** 31, 0), (2 ** 32 - 1, 1)):
+        with pytest.raises(ValueError):
+            orc.key(9, sample, replica)
+        with pytest.raises(ValueError):
+            orc.init_spins(4, 9, sample, replica)
+        with pytest.raises(ValueError):
+            orc.init_spin_sites([0, 1], 9, sample, replica)
+    for sample in (2 ** 31, 2 ** 32 - 1):
+        with pytest.raises(ValueError):
+            orc.gaussian_couplings(4, 9, sample)
+        with pytest.raises(ValueError):
+            orc.gaussian_coupling_sites([0], 9, sample)
+
+
 # --------------------------------------------------------------------------
 # Initial spins
 # --------------------------------------------------------------------------
