@@ -98,6 +98,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg")
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default pool launch shape")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default line: skip the batched-pool summary (512 samples x 2 replicas)")
+    ap.add_argument("--no-serving", action="store_true", help="default line: skip the serving summary")
     return ap.parse_args()
 
 
@@ -387,6 +390,12 @@ def run_ours(args, wl):
     hsg.hsg_profile(lat.ctx, False)
     e_last = float(lat.energy_log()[-1]) if wl["energy_every"] else float("nan")
     elapsed_ms = hdist.max_over_ranks(elapsed_ms, device="cuda")
+    # The oracle leg, part 1 (outside every timed region): the error of the
+    # reported quantities against the FP64 oracle, on this lattice as the
+    # timed steps left it.
+    errors = None
+    if world == 1 and not args.no_cpu_baseline:
+        errors = errors_vs_oracle(hsg, lat, J, wl, e_last)
 
     # ---- end to end through the C ABI, from pinned host memory -------------
     # Every step uploads its inputs (couplings and spins, site-major fp32)
@@ -465,22 +474,33 @@ def run_ours(args, wl):
     b_hb = BYTES_HB_PACKED if packed else BYTES_HB
     roof = None
     if or_n:
-        alg = units * b_or
+        # `achieved` prices each site update at the per-update byte model of
+        # the update kind (72 B for over-relaxation with float4 spins, 60 B
+        # packed), whatever the kernel actually moves: a temporally blocked
+        # sweep that moves fewer bytes shows as a fraction above 1.  The
+        # kernel's own 44 B model and the DRAM bytes ncu counted for it are
+        # given beside it, each against the measured copy peak and the
+        # nominal 8 TB/s.
         avg_s = or_ms / or_n / 1e3
+        b_model = BYTES_OR_PACKED if packed else BYTES_OR
+        alg = units * b_model
         ach = alg / avg_s / 1e9
         kname = ("over-relaxation full sweep, temporally blocked" if wave else
                  "over-relaxation half-sweep, packed spins" if packed else "over-relaxation half-sweep")
-        roof = {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1),
-                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
-                "traffic": profiled_traffic(variant, L), "algorithmic_bytes_per_launch": alg,
+        traffic = profiled_traffic(variant, L)
+
+        def rate(nbytes):
+            g = nbytes / avg_s / 1e9
+            return {"GBps": round(g, 1), "frac": round(g / peak, 4), "frac_of_nominal_8TBps": round(g / 8000.0, 4)}
+
+        roof = {"bound": "hbm", "kernel": kname, "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_source": f"{peak_kind} hbm_gbs",
+                "byte_model": f"{b_model} B per site update", "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg, "units_per_launch": units,
                 "avg_launch_ms": round(or_ms / or_n, 5), "launches": or_n,
                 "frac_of_nominal_8TBps": round(ach / 8000.0, 4),
-                # The rate the single-pass byte model (72 B per site update,
-                # one pass per colour) would need for the same sweep time.
-                "single_pass_equivalent": ({"bytes_per_update": BYTES_OR,
-                                            "GBps": round(units * BYTES_OR / avg_s / 1e9, 1),
-                                            "frac": round(units * BYTES_OR / avg_s / 1e9 / peak, 4)}
-                                           if wave or packed else None),
+                "blocked_44B_model": dict(rate(units * BYTES_OR_WAVE), bytes_per_update=BYTES_OR_WAVE) if wave else None,
+                "dram_measured": dict(rate(traffic), bytes_per_launch=traffic) if traffic else None,
                 "measured_over": f"{args.steps} steps with per-launch CUDA events ({profiled_ms / args.steps:.3f} "
                                  f"ms/step, directly launched)"}
     if met_n and met_ms > or_ms + hb_ms:
@@ -525,7 +545,33 @@ def run_ours(args, wl):
         "energy_per_spin_last": e_last,
         "paper_context": PAPER_CONTEXT,
     }
+    if world == 1 and args.workload == "l256_hb_or":
+        # the batched and served forms of the path, measured in the same run
+        # (after the lattice above is released): compact summaries
+        if not args.no_batched:
+            b = measure_batched(steps=20, warmup=3)
+            out["batched"] = {k: b[k] for k in ("value", "unit", "speedup_vs_plain", "plain_one_lattice_per_launch",
+                                                "hit_updates_per_ns", "lattices", "sites", "autotuned",
+                                                "gpu_launches")}
+            out["batched"]["workload"] = BATCH["desc"]
+        if not args.no_serving:
+            m = measure_serving()
+            o, sub, fifo, same = (m["overload"], m["sub_saturating"], m["plain_fifo_one_per_launch"],
+                                  m["served_same_trace"])
+            out["serving"] = {
+                "workload": SERVE["desc"],
+                "overload": {k: o[k] for k in ("requests", "rate_req_per_s", "updates_per_ns",
+                                               "offered_updates_per_ns", "p50_ms", "p99_ms", "completed",
+                                               "wall_s", "max_batch")},
+                "sub_saturating": {k: sub[k] for k in ("requests", "rate_req_per_s", "updates_per_ns", "p50_ms",
+                                                       "p99_ms", "max_batch")},
+                "same_trace_served_vs_plain_fifo": {
+                    "requests": same["requests"], "rate_req_per_s": fifo["rate_req_per_s"],
+                    "served": {k: same[k] for k in ("p50_ms", "p99_ms", "updates_per_ns")},
+                    "plain_fifo_one_per_launch": {k: fifo[k] for k in ("p50_ms", "p99_ms", "updates_per_ns")}},
+            }
     if world == 1 and not args.no_cpu_baseline:
+        out["errors_vs_oracle"] = errors
         out["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(out), flush=True)
     if world > 1:
@@ -548,6 +594,107 @@ def _oracle_setup(wl):
     p = oracle.Params(key=oracle.key(wl["seed"]), sweep=0, beta=1.0 / wl["T"], step=wl["step"], hits=wl["hits"],
                       proposal=oracle.PROP_BALL if wl["proposal"] == "BALL" else oracle.PROP_SPHERE)
     return oracle, L, J, s, kind, p
+
+
+def _sample_sites(L, rng, colour, n):
+    """n random sites of one colour plus the lattice's corners."""
+    cand = rng.integers(0, L ** 3, size=4 * n)
+    x, y, z = cand % L, (cand // L) % L, cand // (L * L)
+    pick = [int(i) for i in cand[(x + y + z) % 2 == colour][:n]]
+    corners = [0, L - 1, L * L - 1, L ** 3 - 1, (L - 1) * L * L, L * (L - 1)]
+    return pick + [i for i in corners if (i % L + (i // L) % L + i // (L * L)) % 2 == colour]
+
+
+def _site_errors(oracle, L, J, before, after, sites, upd, colour, p):
+    """Per-site error of one GPU half-sweep layer against the oracle's update
+    of each listed site from the same state `before` (fp32 values in fp64).
+    The parity rules of the tests: heat-bath sites within 1e-5 (relative)
+    of the h_z = 0 plane and Metropolis sites within 1e-5 of a threshold are
+    excluded (fp32 and fp64 may take different branches there); a site is
+    counted as ill-conditioned when 4 kappa > 1e-5, kappa = 2^-24 sum|J| /
+    |h| (its fp32 field's round-off relative to the field)."""
+    u = 2.0 ** -24
+    err_all, err_well, over_kappa = [], [], []
+    excluded = ill = 0
+    for i in sites:
+        x, y, zc = i % L, (i // L) % L, i // (L * L)
+        h = oracle.local_field(L, J, before, i)
+        hn = float(np.linalg.norm(h))
+        want, margin = oracle.update_site(upd, before[3 * i: 3 * i + 3], h, p, i, colour)
+        if (upd == oracle.HB and abs(h[2]) < 1e-5 * hn) or (upd == oracle.MET and margin < 1e-5):
+            excluded += 1
+            continue
+        bonds = [J[3 * i], J[3 * i + 1], J[3 * i + 2], J[3 * ((x - 1) % L + y * L + zc * L * L)],
+                 J[3 * (x + ((y - 1) % L) * L + zc * L * L) + 1], J[3 * (x + y * L + ((zc - 1) % L) * L * L) + 2]]
+        kappa = u * float(np.sum(np.abs(bonds))) / max(hn, 1e-300)
+        e = float(np.max(np.abs(after[3 * i: 3 * i + 3] - want)))
+        err_all.append(e)
+        over_kappa.append(e / kappa)
+        if 4 * kappa <= 1e-5:
+            err_well.append(e)
+        else:
+            ill += 1
+    return {"sites": len(sites), "excluded": excluded, "ill_conditioned": ill,
+            "max_abs_err": max(err_all), "max_abs_err_well_conditioned": max(err_well),
+            "max_err_over_kappa": round(max(over_kappa), 3)}
+
+
+def errors_vs_oracle(hsg, lat, J32, wl, e_last):
+    """The error of each reported quantity against the FP64 oracle, measured
+    after the timed region on the benchmark's own lattice (the oracle leg):
+    the logged E/N against the oracle's energy of the same spins; one
+    main-update half-sweep (colour 0) and one over-relaxation sweep of the
+    kernel the benchmark times (colour 0 from the state before it, colour 1
+    from the GPU's own new colour 0) at >= 3000 sampled sites per layer; and
+    the FP64 renormalisation of the whole lattice against the oracle's."""
+    import oracle
+
+    oracle.build()
+    L, N = wl["L"], wl["L"] ** 3
+    J = J32.astype(np.float64)
+    rng = np.random.default_rng(7)
+    out = {"rules": "max |diff| per spin component at each sampled site; heat-bath frame-branch band and "
+                    "Metropolis near-threshold sites excluded; ill-conditioned = 4 kappa > 1e-5, kappa = "
+                    "2^-24 sum|J| / |h|"}
+    s_end = lat.spins().astype(np.float64)
+    if wl["energy_every"]:
+        e_ref = oracle.energy(L, J, s_end) / N
+        out["energy_per_spin"] = {"gpu": e_last, "oracle": e_ref, "abs_err": abs(e_last - e_ref)}
+    # FP64 renormalisation of the current state against the oracle's
+    lat.renorm()
+    got = lat.spins().astype(np.float64)
+    ref = s_end.copy()
+    oracle.renorm(L, ref)
+    norms = np.linalg.norm(got.reshape(-1, 3), axis=1)
+    out["renorm"] = {"sites": N, "max_abs_err": float(np.max(np.abs(got - ref))),
+                     "max_norm_deviation": float(np.max(np.abs(norms - 1.0)))}
+    # one main-update half-sweep on colour 0
+    upd = {"HB": oracle.HB, "MET": oracle.MET}.get(wl["kind"])
+    if upd is not None:
+        sched = hsg.schedule(kind=hsg.HSG_HEATBATH if upd == oracle.HB else hsg.HSG_METROPOLIS, hits=wl["hits"],
+                             proposal=hsg.HSG_PROP_BALL if wl["proposal"] == "BALL" else hsg.HSG_PROP_SPHERE,
+                             step=wl["step"], T=wl["T"])
+        before = got
+        sweep = lat.sweep_count
+        lat.half_sweep(sched, sched.kind, 0)
+        got = lat.spins().astype(np.float64)
+        p = oracle.Params(key=oracle.key(wl["seed"]), sweep=sweep, beta=1.0 / wl["T"], step=wl["step"],
+                          hits=wl["hits"], proposal=oracle.PROP_BALL if wl["proposal"] == "BALL" else
+                          oracle.PROP_SPHERE)
+        name = "heatbath_half_sweep" if upd == oracle.HB else "metropolis_half_sweep"
+        out[name] = _site_errors(oracle, L, J, before, got, _sample_sites(L, rng, 0, 3000), upd, 0, p)
+    # one over-relaxation sweep with the kernel the benchmark's OR sweeps use
+    if wl["n_or"]:
+        before = got
+        lat.sweep(hsg.schedule(kind=hsg.HSG_NONE, n_or=1, kernel=hsg.HSG_KERNEL_AUTO), 1)
+        got = lat.spins().astype(np.float64)
+        mid = np.where(np.repeat(np.indices((L, L, L)).sum(axis=0).reshape(-1) % 2 == 0, 3), got, before)
+        p = oracle.Params()
+        out["overrelax_sweep"] = {
+            "colour0": _site_errors(oracle, L, J, before, got, _sample_sites(L, rng, 0, 3000), oracle.OR, 0, p),
+            "colour1_from_gpu_colour0": _site_errors(oracle, L, J, mid, got, _sample_sites(L, rng, 1, 3000),
+                                                     oracle.OR, 1, p)}
+    return out
 
 
 def _oracle_sample_sweep(oracle, L, J, s, kind, p, i0, i1):
@@ -662,15 +809,13 @@ def batch_specs():
     return out
 
 
-def run_batched(args):
+def measure_batched(steps: int, warmup: int, autotune: bool = True) -> dict:
+    """The batched workload in one pool (graph-replayed sweeps, autotuned
+    launch shape) against one lattice per launch, on the current device."""
     import torch
 
-    from paper_1006_2566_gb300 import build
-
-    build.build()
     from paper_1006_2566_gb300 import hsg
 
-    torch.cuda.set_device(0)
     specs = batch_specs()
     sites = sum(L ** 3 for L, *_ in specs)
     sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=BATCH["hits"], proposal=hsg.HSG_PROP_BALL, step=BATCH["step"],
@@ -683,26 +828,26 @@ def run_batched(args):
         for spec in specs:
             pool.admit(*spec)
         t0 = time.perf_counter()
-        if args.no_autotune:
+        if not autotune:
             cfg = (256, 512, 8, 0)  # the pool's default launch configuration
             hsg.hsg_pool_config(pool.pool, *cfg)
         else:
             cfg = hsg.hsg_pool_autotune(pool.pool, sched)
         tune_s = time.perf_counter() - t0
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             pool.sweep(sched, sps)
         torch.cuda.synchronize()
         n0 = hsg.hsg_pool_launch_count(pool.pool)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             pool.sweep(sched, sps)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         launches = hsg.hsg_pool_launch_count(pool.pool) - n0
         energies = pool.energies()
-    value = sites * passes * sps * args.steps / (ms * 1e6)
+    value = sites * passes * sps * steps / (ms * 1e6)
     # one lattice per launch: every lattice of a representative subset swept
     # on its own context, one after another
     sub = specs[:: max(1, len(specs) // 64)]
@@ -726,22 +871,37 @@ def run_batched(args):
     for lat, _ in ctxs:
         lat.close()
     plain = sub_sites * passes * sps / (plain_ms * 1e6)
+    return {"value": round(value, 4), "unit": "spin updates/ns", "steps": steps, "ms_per_step": round(ms / steps, 4),
+            "lattices": len(specs), "sites": sites,
+            "autotuned": {"threads": cfg[0], "tile_sites": cfg[1], "blocks_per_sm": cfg[2],
+                          "hits_per_pass": cfg[3] or BATCH["hits"], "seconds": round(tune_s, 3)} if autotune else None,
+            "hit_updates_per_ns": round(sites * (BATCH["hits"] + BATCH["n_or"]) * sps * steps / (ms * 1e6), 4),
+            "plain_one_lattice_per_launch": {"value": round(plain, 4), "unit": "spin updates/ns",
+                                             "lattices": len(sub), "sites": sub_sites,
+                                             "ms_for_10_sweeps": round(plain_ms, 3)},
+            "speedup_vs_plain": round(value / plain, 2), "gpu_launches": int(launches),
+            "energy_per_spin_mean": float(np.nanmean(energies))}
+
+
+def run_batched(args):
+    import torch
+
+    from paper_1006_2566_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    b = measure_batched(args.steps, args.warmup, not args.no_autotune)
     out = {
-        "metric": "spin updates/ns", "value": round(value, 4), "unit": "spin updates/ns", "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "metric": "spin updates/ns", "value": b["value"], "unit": "spin updates/ns", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: seeded sides and temperatures, couplings and spins from Philox",
-        "config": {"workload": BATCH["desc"], "lattices": len(specs), "sites": sites,
-                   "autotuned": {"threads": cfg[0], "tile_sites": cfg[1], "blocks_per_sm": cfg[2],
-                                 "hits_per_pass": cfg[3] or BATCH["hits"],
-                                 "seconds": round(tune_s, 3)}},
-        "hit_updates_per_ns": round(sites * (BATCH["hits"] + BATCH["n_or"]) * sps * args.steps / (ms * 1e6), 4),
-        "plain_one_lattice_per_launch": {"value": round(plain, 4), "unit": "spin updates/ns",
-                                         "lattices": len(sub), "sites": sub_sites,
-                                         "ms_for_10_sweeps": round(plain_ms, 3)},
-        "speedup_vs_plain": round(value / plain, 2),
-        "gpu_launches": int(launches),
-        "energy_per_spin_mean": float(np.nanmean(energies)),
+        "config": {"workload": BATCH["desc"], "lattices": b["lattices"], "sites": b["sites"],
+                   "autotuned": b["autotuned"]},
+        "hit_updates_per_ns": b["hit_updates_per_ns"],
+        "plain_one_lattice_per_launch": b["plain_one_lattice_per_launch"],
+        "speedup_vs_plain": b["speedup_vs_plain"], "gpu_launches": b["gpu_launches"],
+        "energy_per_spin_mean": b["energy_per_spin_mean"],
     }
     print(json.dumps(out), flush=True)
 
@@ -757,27 +917,28 @@ SERVE = dict(rate=2000.0, n_overload=800, n_sub=300, n_plain=100, seed=5, budget
                    "frees; continuous batching"))
 
 
-def run_serving(args):
+def measure_serving(n_overload: int = SERVE["n_overload"], n_sub: int = SERVE["n_sub"],
+                    n_plain: int = SERVE["n_plain"]) -> dict:
+    """The serving workload on the current device: an overload trace at the
+    configured rate (throughput against offered load), a sub-saturating
+    trace at 0.6 x the measured capacity, and its first n_plain requests
+    both served and one per launch in arrival order (p50/p99 side by side)."""
     import torch
 
-    from paper_1006_2566_gb300 import build
-
-    build.build()
     from paper_1006_2566_gb300 import hsg, serve
 
-    torch.cuda.set_device(0)
     kw = dict(kind=hsg.HSG_METROPOLIS, hits=4, proposal=hsg.HSG_PROP_BALL, step=0.5, n_or=2, renorm_every=10)
     stream = torch.cuda.Stream()
     # warm-up: a short trace (builds graphs, pages in the arena)
     serve.serve(serve.poisson_trace(40, SERVE["rate"], seed=99, first_sample=10 ** 6), kw, SERVE["budget"],
                 SERVE["max_slots"], stream)
-    over = serve.poisson_trace(SERVE["n_overload"], SERVE["rate"], seed=SERVE["seed"])
+    over = serve.poisson_trace(n_overload, SERVE["rate"], seed=SERVE["seed"])
     res_o, st_o = serve.serve(over, kw, SERVE["budget"], SERVE["max_slots"], stream)
     capacity = st_o.completed / st_o.wall_seconds  # requests per second at saturation
     sub_rate = 0.6 * capacity
-    sub = serve.poisson_trace(SERVE["n_sub"], sub_rate, seed=SERVE["seed"] + 1, first_sample=10 ** 5)
+    sub = serve.poisson_trace(n_sub, sub_rate, seed=SERVE["seed"] + 1, first_sample=10 ** 5)
     res_s, st_s = serve.serve(sub, kw, SERVE["budget"], SERVE["max_slots"], stream)
-    plain_trace = sub[: SERVE["n_plain"]]
+    plain_trace = sub[:n_plain]
     res_p, st_p = serve.serve_fifo(plain_trace, kw, stream)
     res_b, st_b = serve.serve(plain_trace, kw, SERVE["budget"], SERVE["max_slots"], stream)
     passes = 3
@@ -788,16 +949,28 @@ def run_serving(args):
                 "p50_ms": round(st.p50_ms, 2), "p99_ms": round(st.p99_ms, 2), "mean_ms": round(st.mean_ms, 2),
                 "max_batch": st.max_batch, "ticks": st.ticks}
 
-    out = {
-        "metric": "spin updates/ns", "value": round(st_o.updates_per_ns, 4), "unit": "spin updates/ns", "n_gpus": 1,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic: seeded Poisson trace; couplings and spins from Philox",
-        "config": {"workload": SERVE["desc"]},
+    return {
         "overload": dict(block(st_o), offered_updates_per_ns=round(offered, 2), rate_req_per_s=SERVE["rate"],
                          requests=len(over)),
         "sub_saturating": dict(block(st_s), rate_req_per_s=round(sub_rate, 1), requests=len(sub)),
         "plain_fifo_one_per_launch": dict(block(st_p), requests=len(plain_trace), rate_req_per_s=round(sub_rate, 1)),
         "served_same_trace": dict(block(st_b), requests=len(plain_trace)),
+    }
+
+
+def run_serving(args):
+    import torch
+
+    from paper_1006_2566_gb300 import build
+
+    build.build()
+    torch.cuda.set_device(0)
+    m = measure_serving()
+    out = {
+        "metric": "spin updates/ns", "value": m["overload"]["updates_per_ns"], "unit": "spin updates/ns",
+        "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded Poisson trace; couplings and spins from Philox",
+        "config": {"workload": SERVE["desc"]}, **m,
     }
     print(json.dumps(out), flush=True)
 

@@ -19,3 +19,17 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With HSG_PARITY_REPORT set to a path, write what the parity checks
+    measured (per check: sites compared, sites excluded by the rules,
+    ill-conditioned sites, max errors) there as JSON."""
+    path = os.environ.get("HSG_PARITY_REPORT")
+    rules = sys.modules.get("parity_rules")
+    if not path or rules is None:
+        return
+    import json
+
+    with open(path, "w") as f:
+        json.dump(rules.REPORT, f, indent=0)

@@ -1,22 +1,14 @@
 """GPU path vs the FP64 oracle, through the C ABI (needs a CUDA GPU).
 
-Tolerances (written per test):
-  * half-sweeps: max |diff| <= 1e-5 per spin component at every site whose
-    fp32 local field is well conditioned, 4 kappa <= 1e-5 with
-    kappa = 2^-24 * sum_k |J_k| / |h| (the field's fp32 round-off relative
-    to its length, which the update's direction inherits).  At the rare
-    sites with a nearly cancelling field (<= 0.1 %) the difference must
-    stay within 1e-5 + 64 kappa, the propagated round-off bound;
-  * Metropolis: sites whose accept decisions lie within 1e-5 of their
-    threshold (|u3 - exp(-beta dE)| < 1e-5, margin reported by the oracle)
-    are excluded: fp32 and fp64 may decide differently there;
-  * heat-bath: sites whose field is within 1e-5 (relative) of the h_z = 0
-    plane are excluded: the orthonormal frame of the azimuth switches
-    branch there and fp32/fp64 may pick different branches;
-  * energies: |E/N difference| <= 2e-6 (per-site terms are fp32);
-  * long runs: mean E/N within 3 sigma (binned errors of both runs).
-Every half-sweep starts the GPU and the oracle from the same state (fp32
-values, the oracle holding them in fp64) and the same fp32-rounded J.
+The tolerances are the parity rules of tests/parity_rules.py: per site and
+per half-sweep layer, 1e-5 per spin component, Metropolis sites within 1e-5
+of a threshold and heat-bath sites in the frame-branch band left out, the
+other colour bit-identical; whole sweeps are checked layer by layer, each
+layer of the oracle starting from the GPU's own state before it.  Energies:
+|E/N difference| <= 2e-6 (per-site terms are fp32).  Long runs: mean E/N
+within 3 sigma (binned errors of both runs).  Every half-sweep starts the
+GPU and the oracle from the same state (fp32 values, the oracle holding them
+in fp64) and the same fp32-rounded J.
 """
 import ctypes
 import math
@@ -32,6 +24,8 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_1006_2566_gb300 import inputs  # noqa: E402
+from parity_rules import (check_half_sweep, check_layer, check_or_sweep, colour_mask, frame_band,  # noqa: E402
+                          record)
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 TOL = 1e-5
@@ -66,49 +60,6 @@ def oracle_state(L, seed_j, seed_s):
     J = inputs.gaussian_couplings(L, seed=seed_j)
     s32 = inputs.random_spins(L, seed=seed_s, dtype=np.float32)
     return J, s32
-
-
-U32 = 2.0 ** -24
-
-
-def colour_mask(L, c):
-    g = np.indices((L, L, L))
-    return (((g[0] + g[1] + g[2]) % 2) == c).reshape(-1)
-
-
-def bond_sums(L, J):
-    """sum of |J| over the six bonds of every site."""
-    a = np.abs(J.reshape(L, L, L, 3))  # [z, y, x, d]
-    s = a.sum(axis=3)
-    s += np.roll(a[..., 0], 1, axis=2) + np.roll(a[..., 1], 1, axis=1) + np.roll(a[..., 2], 1, axis=0)
-    return s.reshape(-1)
-
-
-def check_half_sweep(L, Jr, before64, got, ref, colour, exclude=None):
-    """Compare one half-sweep site by site (see the module docstring).
-    Returns (number of ill-conditioned sites, max err/kappa)."""
-    idx = np.nonzero(colour_mask(L, colour))[0]
-    h = np.array([oracle.local_field(L, Jr, before64, int(i)) for i in idx])
-    hn = np.linalg.norm(h, axis=1)
-    kappa = U32 * bond_sums(L, Jr)[idx] / np.maximum(hn, 1e-300)
-    err = np.max(np.abs(got - ref).reshape(-1, 3)[idx], axis=1)
-    skip = np.zeros(len(idx), bool) if exclude is None else exclude[idx]
-    well = (4 * kappa <= TOL) & ~skip
-    ill = ~well & ~skip
-    assert np.all(err[well] <= TOL), float(np.max(err[well]))
-    assert ill.sum() <= max(2, 0.001 * len(idx)), int(ill.sum())
-    assert np.all(err[ill] <= TOL + 64 * kappa[ill])
-    keep = ~skip
-    return int(ill.sum()), float(np.max(err[keep] / kappa[keep])) if keep.any() else 0.0
-
-
-def frame_band(L, Jr, before64, colour):
-    """Sites whose field lies within 1e-5 (relative) of the h_z = 0 plane."""
-    band = np.zeros(L ** 3, bool)
-    for i in np.nonzero(colour_mask(L, colour))[0]:
-        h = oracle.local_field(L, Jr, before64, int(i))
-        band[i] = abs(h[2]) < TOL * np.linalg.norm(h)
-    return band
 
 
 # ---------------------------------------------------------------------------
@@ -188,12 +139,7 @@ def test_over_relaxation_half_sweep_parity(hsg, variant, L):
     sched = hsg.schedule(kernel=variant)
     for colour in (0, 1):
         got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_OVERRELAX, colour, sched)
-        before = s32.astype(np.float64)
-        ref = before.copy()
-        oracle.half_sweep(L, Jr, ref, oracle.OR, colour, oracle.Params())
-        check_half_sweep(L, Jr, before, got, ref, colour)
-        other = ~colour_mask(L, colour)
-        assert np.array_equal(got.reshape(-1, 3)[other], s32.astype(np.float64).reshape(-1, 3)[other])
+        check_layer(L, Jr, s32, got, oracle.OR, colour, oracle.Params(), label=f"OR half-sweep L={L} v{variant}")
 
 
 MET_CASES = [
@@ -218,16 +164,11 @@ def test_metropolis_half_sweep_parity(hsg, variant, case):
     beta = 0.0 if math.isinf(T) else 1.0 / T
     for colour in (0, 1):
         got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_METROPOLIS, colour, sched, seed=11, sweep=3)
-        before = s32.astype(np.float64)
-        ref = before.copy()
         p = oracle.Params(key=oracle.key(11), sweep=3, beta=beta, step=0.5, hits=hits, proposal=proposal)
-        margins = oracle.half_sweep(L, Jr, ref, oracle.MET, colour, p, want_margins=True)
-        mask = colour_mask(L, colour)
-        near = mask & (margins < TOL)
-        assert near.sum() <= max(2, 0.002 * mask.sum())
-        check_half_sweep(L, Jr, before, got, ref, colour, exclude=near)
-        moved = np.any(ref.reshape(-1, 3) != s32.astype(np.float64).reshape(-1, 3), axis=1)
-        assert moved[mask].mean() > 0.05  # the chain does move
+        check_layer(L, Jr, s32, got, oracle.MET, colour, p,
+                    label=f"Metropolis half-sweep L={L} prop={proposal} hits={hits} T={T} v{variant}")
+        moved = np.any(got.reshape(-1, 3) != s32.astype(np.float64).reshape(-1, 3), axis=1)
+        assert moved[colour_mask(L, colour)].mean() > 0.05  # the chain does move
 
 
 FUSED_CASES = [(16, 0, 1, 1.0), (24, 1, 4, 0.5), (40, 1, 2, 0.3)]
@@ -244,13 +185,9 @@ def test_fused_metropolis_or_half_sweep_parity(hsg, variant, case):
     sched = hsg.schedule(kind=hsg.HSG_METROPOLIS_OR, hits=hits, proposal=proposal, step=0.5, T=T, kernel=variant)
     for colour in (0, 1):
         got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_METROPOLIS_OR, colour, sched, seed=31, sweep=4)
-        before = s32.astype(np.float64)
-        ref = before.copy()
         p = oracle.Params(key=oracle.key(31), sweep=4, beta=1.0 / T, step=0.5, hits=hits, proposal=proposal)
-        margins = oracle.half_sweep(L, Jr, ref, oracle.MET_OR, colour, p, want_margins=True)
-        near = colour_mask(L, colour) & (margins < TOL)
-        assert near.sum() <= max(2, 0.002 * colour_mask(L, colour).sum())
-        check_half_sweep(L, Jr, before, got, ref, colour, exclude=near)
+        check_layer(L, Jr, s32, got, oracle.MET_OR, colour, p,
+                    label=f"fused Metropolis+OR half-sweep L={L} hits={hits} T={T} v{variant}")
 
 
 def test_fused_long_run_energy_statistics_match_oracle(hsg):
@@ -284,15 +221,10 @@ def test_heatbath_half_sweep_parity(hsg, variant, L, T):
     sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=T, kernel=variant)
     beta = 0.0 if math.isinf(T) else 1.0 / T
     for colour in (0, 1):
-        s64 = s32.astype(np.float64)
         got = gpu_half_sweep(hsg, L, J, s32, hsg.HSG_HEATBATH, colour, sched, seed=13, sample=2, sweep=5)
-        ref = s64.copy()
         p = oracle.Params(key=oracle.key(13, 2), sweep=5, beta=beta)
-        oracle.half_sweep(L, Jr, ref, oracle.HB, colour, p)
+        check_layer(L, Jr, s32, got, oracle.HB, colour, p, label=f"heat-bath half-sweep L={L} T={T} v{variant}")
         mask = colour_mask(L, colour)
-        band = frame_band(L, Jr, s64, colour)
-        assert band.sum() <= max(2, 0.001 * mask.sum())
-        check_half_sweep(L, Jr, s64, got, ref, colour, exclude=band)
         assert np.max(np.abs(np.linalg.norm(got.reshape(-1, 3)[mask], axis=1) - 1)) < 1e-5
 
 
@@ -435,57 +367,128 @@ def test_sweep_is_the_composition_of_half_sweeps(hsg, variant, kind):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-def test_over_relaxation_sweep_matches_oracle(hsg, variant):
+@pytest.mark.parametrize("L", [24, 40])
+def test_over_relaxation_sweep_matches_oracle(hsg, variant, L):
     """One over-relaxation sweep (colour 0, then colour 1) from the same
-    state through hsg_sweep.  Colour 0 is checked site by site as in the
-    half-sweep tests; colour 1 is computed from colour-0 values that already
-    carry fp32 round-off, so 99.5 % of its sites must agree to 1e-5 and all
-    of them to 1e-3."""
-    L = 24
-    J, s32 = oracle_state(L, 900, 901)
+    state through hsg_sweep, every site of both layers under the half-sweep
+    rules: colour 0 against the oracle's half-sweep of the start state,
+    colour 1 against the oracle's half-sweep of the GPU's own new colour 0
+    (the state the GPU's colour-1 layer started from)."""
+    J, s32 = oracle_state(L, 900 + L, 901 + L)
     Jr = inputs.round_to_f32(J)
     with hsg.Lattice(L, 17) as lat:
         lat.set_couplings(J)
         lat.set_spins(s32)
         lat.sweep(hsg.schedule(kind=hsg.HSG_NONE, n_or=1, kernel=variant), 1)
-        got = lat.spins().astype(np.float64)
-    before = s32.astype(np.float64)
-    mid = before.copy()
-    oracle.half_sweep(L, Jr, mid, oracle.OR, 0, oracle.Params())
-    ref = mid.copy()
-    oracle.half_sweep(L, Jr, ref, oracle.OR, 1, oracle.Params())
-    c0 = colour_mask(L, 0)
-    got_mid = np.where(np.repeat(c0, 3), got, before)
-    check_half_sweep(L, Jr, before, got_mid, mid, 0)
-    err1 = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)[~c0]
-    assert np.mean(err1 <= TOL) >= 0.995
-    assert np.max(err1) <= 1e-3
+        got = lat.spins()
+    check_or_sweep(L, Jr, s32, got, label=f"OR sweep L={L} v{variant}")
+
+
+def layered_run(hsg, lat, sched, main, n_or, n_sweeps, renorm_every, energy_every):
+    """The GPU's state after every layer of `n_sweeps` sweeps, issued as
+    half-sweeps one by one (bit-identical to hsg_sweep, tested above):
+    a list of (layer, state before, state after) and the E/N values the
+    schedule logs, with the state each was computed from."""
+    layers, energies = [], []
+    cur = lat.spins()
+    for _ in range(n_sweeps):
+        sw = lat.sweep_count
+        steps = ([(main, c) for c in (0, 1)] if main is not None else []) + [(hsg.HSG_OVERRELAX, c) for _ in range(n_or)
+                                                                            for c in (0, 1)]
+        for upd, c in steps:
+            lat.half_sweep(sched, upd, c)
+            nxt = lat.spins()
+            layers.append(((upd, c, sw), cur, nxt))
+            cur = nxt
+        lat.sweep_count = sw + 1
+        if renorm_every and (sw + 1) % renorm_every == 0:
+            lat.renorm()
+            nxt = lat.spins()
+            layers.append((("renorm", None, sw), cur, nxt))
+            cur = nxt
+        if energy_every and (sw + 1) % energy_every == 0:
+            energies.append((lat.energy(), cur))
+    return layers, energies
+
+
+ORACLE_UPD = {1: oracle.MET, 2: oracle.HB, 3: oracle.OR, 4: oracle.MET_OR}
+
+
+def check_layers(L, Jr, layers, params_of, label):
+    """Every layer of a layered_run against the oracle's same layer from the
+    GPU's state before it (renormalisation: within 2^-24 of the fp64
+    result)."""
+    for (upd, c, sw), before, after in layers:
+        if upd == "renorm":
+            ref = before.astype(np.float64)
+            oracle.renorm(L, ref)
+            err = float(np.max(np.abs(after.astype(np.float64) - ref)))
+            record(label=f"{label} renorm sweep {sw}", L=L, max_err=err)
+            assert err <= 2 ** -24
+            continue
+        check_layer(L, Jr, before, after, ORACLE_UPD[upd], c, params_of(sw), label=f"{label} sweep {sw} upd {upd} c{c}")
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_sweep_schedule_energy_log_matches_oracle(hsg, variant):
     """Two sweeps of heat-bath + 2 OR with renormalisation and E/N every
-    sweep: the energy log agrees with the oracle's to 1e-5 and the median
-    spin to 1e-5 (the per-spin differences compound through the 12
-    half-sweep layers; per-layer parity is checked by the half-sweep tests,
-    the exact order by test_sweep_is_the_composition_of_half_sweeps)."""
+    sweep (12 half-sweep layers and 2 renormalisations): every layer is
+    checked against the oracle's same layer from the GPU's state before it,
+    every logged E/N against the oracle's energy of the state it was
+    computed from (2e-6), the layered run against hsg_sweep bit for bit,
+    and the log against the oracle's own two-sweep run (1e-5: its states
+    differ from the GPU's by the round-off of 12 layers)."""
     L = 16
     J = inputs.gaussian_couplings(L, seed=17)
+    Jr = inputs.round_to_f32(J)
     sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=0.8, n_or=2, renorm_every=1, energy_every=1, kernel=variant)
     with hsg.Lattice(L, 17) as lat:
         lat.set_couplings(J)
         s0 = lat.spins().astype(np.float64)
         lat.sweep(sched, 2)
-        got = lat.spins().astype(np.float64)
+        want = lat.spins()
         elog = lat.energy_log()
         assert lat.sweep_count == 2
+    with hsg.Lattice(L, 17) as lat:
+        lat.set_couplings(J)
+        layers, energies = layered_run(hsg, lat, sched, hsg.HSG_HEATBATH, 2, 2, 1, 1)
+        assert np.array_equal(lat.spins(), want)
+    assert len(layers) == 14 and len(energies) == 2 == len(elog)
+    check_layers(L, Jr, layers, lambda sw: oracle.Params(key=oracle.key(17), sweep=sw, beta=1 / 0.8),
+                 f"HB+2OR schedule L={L} v{variant}")
+    for (e, state), logged in zip(energies, elog):
+        assert e == logged
+        ref = oracle.energy(L, Jr, state.astype(np.float64)) / L ** 3
+        record(label=f"energy log L={L} v{variant}", max_err=abs(e - ref))
+        assert abs(e - ref) <= 2e-6
     s = s0.copy()
     sch = oracle.Schedule(kind=oracle.HB, beta=1 / 0.8, n_or=2, renorm_every=1, energy_every=1)
-    sw, ref_log = oracle.sweeps(L, inputs.round_to_f32(J), s, sch, oracle.key(17), 2)
-    assert sw == 2 and len(elog) == 2
+    sw, ref_log = oracle.sweeps(L, Jr, s, sch, oracle.key(17), 2)
+    assert sw == 2
     assert np.max(np.abs(elog - ref_log)) < 1e-5
-    err = np.max(np.abs(got - s).reshape(-1, 3), axis=1)
-    assert np.median(err) <= TOL
+
+
+@pytest.mark.parametrize("kind", ["MET", "METOR"])
+def test_metropolis_sweeps_layer_by_layer(hsg, kind):
+    """Three sweeps of 3-hit ball Metropolis (or the fused pass) + 1 OR with
+    renormalisation every 2 sweeps, L = 24: every layer against the oracle
+    from the GPU's state before it, and the layered run equal to hsg_sweep."""
+    L = 24
+    J = inputs.gaussian_couplings(L, seed=29)
+    Jr = inputs.round_to_f32(J)
+    k = hsg.HSG_METROPOLIS if kind == "MET" else hsg.HSG_METROPOLIS_OR
+    sched = hsg.schedule(kind=k, hits=3, proposal=1, step=0.5, T=0.6, n_or=1, renorm_every=2)
+    with hsg.Lattice(L, 29) as lat:
+        lat.set_couplings(J)
+        lat.sweep(sched, 3)
+        want = lat.spins()
+    with hsg.Lattice(L, 29) as lat:
+        lat.set_couplings(J)
+        layers, _ = layered_run(hsg, lat, sched, k, 1, 3, 2, 0)
+        assert np.array_equal(lat.spins(), want)
+    assert len(layers) == 3 * 4 + 1
+    check_layers(L, Jr, layers, lambda sw: oracle.Params(key=oracle.key(29), sweep=sw, beta=1 / 0.6, step=0.5, hits=3,
+                                                         proposal=1), f"{kind}+OR sweeps L={L}")
 
 
 def test_long_run_energy_statistics_match_oracle(hsg):
@@ -638,8 +641,10 @@ def test_gpu_matches_the_golden_fixture(hsg):
     tests/golden/l6_seed21.json (L = 6, seed 21; the fixture's own fp32
     couplings and spins): energy, an over-relaxation, a Metropolis (3 hits,
     ball; every decision of the fixture is >= 5e-4 from its threshold) and a
-    heat-bath half-sweep under the half-sweep rules above, and two sweeps of
-    heat-bath + 1 OR under the whole-sweep rule."""
+    heat-bath half-sweep under the half-sweep rules, and two sweeps of
+    heat-bath + 1 OR: the energy log against the stored one (1e-5, the
+    states of the two runs differing by the round-off of 8 layers) and every
+    layer against the oracle's same layer from the GPU's state before it."""
     import json
 
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "l6_seed21.json")) as f:
@@ -664,12 +669,18 @@ def test_gpu_matches_the_golden_fixture(hsg):
     got = gpu_half_sweep(hsg, L, J, s0, hsg.HSG_HEATBATH, 0, sched, seed=seed, sweep=h["sweep"])
     check_half_sweep(L, J, b64, got, np.array(h["spins"]), 0, exclude=frame_band(L, J, b64, 0))
     w = g["hb_or_two_sweeps"]
+    sched = hsg.schedule(kind=hsg.HSG_HEATBATH, T=w["T"], n_or=w["n_or"], energy_every=1)
     with hsg.Lattice(L, seed) as lat:
         lat.set_couplings(J.astype(np.float32))
         lat.set_spins(s0)
-        lat.sweep(hsg.schedule(kind=hsg.HSG_HEATBATH, T=w["T"], n_or=w["n_or"], energy_every=1), w["sweeps"])
-        got = lat.spins().astype(np.float64)
+        lat.sweep(sched, w["sweeps"])
+        want = lat.spins()
         elog = lat.energy_log()
     assert np.max(np.abs(elog - np.array(w["energy_log"]))) < 1e-5
-    err = np.max(np.abs(got - np.array(w["spins"])).reshape(-1, 3), axis=1)
-    assert np.median(err) <= TOL
+    with hsg.Lattice(L, seed) as lat:  # the same sweeps layer by layer, each against the oracle
+        lat.set_couplings(J.astype(np.float32))
+        lat.set_spins(s0)
+        layers, _ = layered_run(hsg, lat, sched, hsg.HSG_HEATBATH, w["n_or"], w["sweeps"], 0, 1)
+        assert np.array_equal(lat.spins(), want)
+    check_layers(L, J, layers, lambda sw: oracle.Params(key=oracle.key(seed), sweep=sw, beta=1 / w["T"]),
+                 f"golden HB+OR L={L}")

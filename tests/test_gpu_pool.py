@@ -253,3 +253,91 @@ def test_pool_metropolis_hits_split_over_passes_give_the_same_result(hsg, kind):
     for got, spec in zip(outs[0], SPECS):
         want, _ = run_alone(hsg, spec, kw, 3)
         assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------------------
+# Pools against the FP64 oracle
+# ---------------------------------------------------------------------------
+
+ORACLE_SPECS = [  # (L, seed, sample, replica, T, couplings from the host?)
+    (4, 21, 0, 0, 0.5, True),
+    (6, 21, 1, 1, 0.8, False),
+    (24, 21, 2, 0, 0.3, True),
+    (40, 21, 3, 1, 1.0, False),
+    (16, 21, 4, 0, math.inf, True),
+]
+
+
+def oracle_couplings(L, seed, sample, host):
+    """The fp32 couplings a pooled lattice holds: the host array uploaded
+    (rounded to fp32), or the device generator's, which equal the oracle's
+    Box-Muller values rounded to fp32 to within 1 ulp (test above); the
+    oracle is fed the same fp32 values as fp64."""
+    if host:
+        return inputs.round_to_f32(inputs.gaussian_couplings(L, seed=seed + 100 * sample))
+    return oracle.gaussian_couplings(L, seed, sample).astype(np.float32).astype(np.float64)
+
+
+def test_pool_sweeps_match_oracle_layer_by_layer(hsg):
+    """Lattices of uneven L at distinct temperatures in one pool (several
+    tiles for the larger ones, less than one for the smallest, a non-default
+    launch shape): each pool sweep of one update kind -- Metropolis (ball,
+    3 hits), over-relaxation, heat-bath, the fused pass -- checked on every
+    site of every lattice, layer by layer, against the oracle's half-sweeps
+    from that lattice's state before the layer, with its own key, counter
+    and temperature.  A lattice admitted mid-run (next to lattices three
+    sweeps ahead) and the hole left by a retired one are covered, and a
+    composite sweep (Metropolis + 1 OR) in a second pool equals the two
+    checked single-kind sweeps bit for bit."""
+    from parity_rules import check_one_sweep, check_or_sweep
+
+    met = dict(kind=hsg.HSG_METROPOLIS, hits=3, proposal=hsg.HSG_PROP_BALL, step=0.5)
+    kinds = [("MET", met, oracle.MET), ("OR", dict(kind=hsg.HSG_NONE, n_or=1), oracle.OR),
+             ("HB", dict(kind=hsg.HSG_HEATBATH), oracle.HB),
+             ("METOR", dict(met, kind=hsg.HSG_METROPOLIS_OR, hits=2), oracle.MET_OR)]
+    Js = {spec: oracle_couplings(spec[0], spec[1], spec[2], spec[5]) for spec in ORACLE_SPECS}
+    late = (12, 21, 9, 0, 0.6, False)
+    Js[late] = oracle_couplings(*late[:3], late[5])
+
+    def admit(pool, spec):
+        L, seed, sample, replica, T, host = spec
+        return pool.admit(L, seed, sample, replica, T, J=Js[spec] if host else None)
+
+    def check(pool, slots, before, name, kw, upd, sweep_of):
+        for spec, slot in slots.items():
+            L, seed, sample, replica, T, _ = spec
+            after = pool.spins(slot)
+            label = f"pool {name} L={L} T={T} slot {slot}"
+            if upd == oracle.OR:
+                check_or_sweep(L, Js[spec], before[slot], after, label=label)
+            else:
+                p = oracle.Params(key=oracle.key(seed, sample, replica), sweep=sweep_of[slot],
+                                  beta=0.0 if math.isinf(T) else 1.0 / T, step=0.5, hits=kw.get("hits", 1),
+                                  proposal=hsg.HSG_PROP_BALL)
+                check_one_sweep(L, Js[spec], before[slot], after, upd, p, label=label)
+
+    with hsg.Pool(1 << 26, 8, torch.cuda.Stream()) as pool, hsg.Pool(1 << 26, 8, torch.cuda.Stream()) as twin:
+        hsg.hsg_pool_config(pool.pool, 128, 384, 6, 0)
+        slots = {spec: admit(pool, spec) for spec in ORACLE_SPECS}
+        twin_slots = {spec: admit(twin, spec) for spec in ORACLE_SPECS}
+        for spec, slot in slots.items():  # the initial spins: the oracle's Philox map, to fp32 round-off
+            L, seed, sample, replica = spec[:4]
+            assert np.max(np.abs(pool.spins(slot) - oracle.init_spins(L, seed, sample, replica))) < 1e-6
+        twin.sweep(hsg.schedule(**dict(met, n_or=1)), 1)  # one composite sweep
+        for n, (name, kw, upd) in enumerate(kinds):
+            if n == 2:  # retire one lattice and admit a new one into the pool mid-run
+                pool.retire(slots.pop(ORACLE_SPECS[1]))
+                slots[late] = admit(pool, late)
+            before = {slot: pool.spins(slot) for slot in slots.values()}
+            sweep_of = {slot: pool.sweep_count(slot) for slot in slots.values()}
+            pool.sweep(hsg.schedule(**kw), 1)
+            check(pool, slots, before, name, kw, upd, sweep_of)
+            if n == 1:  # Metropolis then OR == the composite sweep of the twin pool
+                for spec, slot in slots.items():
+                    assert np.array_equal(pool.spins(slot), twin.spins(twin_slots[spec])), spec
+        assert pool.sweep_count(slots[late]) == 2 and pool.sweep_count(slots[ORACLE_SPECS[0]]) == 4
+        e = pool.energies()
+        for spec, slot in slots.items():  # E/N of each lattice against the oracle's energy of its state
+            L = spec[0]
+            ref = oracle.energy(L, Js[spec], pool.spins(slot).astype(np.float64)) / L ** 3
+            assert abs(e[slot] - ref) <= 2e-6, spec

@@ -1,13 +1,17 @@
 """The continuous-batching request loop (needs a CUDA GPU): every result is
 the same alone and in the mix; requests wait for memory and are admitted in
-arrival order."""
+arrival order; served results agree with the FP64 oracle."""
+import math
+
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+import oracle  # noqa: E402
 from paper_1006_2566_gb300 import serve  # noqa: E402
+from parity_rules import check_one_sweep, check_or_sweep, record  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -17,6 +21,7 @@ def hsg():
     from paper_1006_2566_gb300 import build
 
     build.build()
+    oracle.build()
     from paper_1006_2566_gb300 import hsg as h
 
     return h
@@ -65,3 +70,47 @@ def test_withdrawn_requests_leave_the_others_unchanged(hsg):
             lat.generate_couplings()
             lat.sweep(hsg.schedule(T=q.T, **kw), q.sweeps)
             assert np.array_equal(r.spins, lat.spins()), q
+
+
+@pytest.mark.parametrize("kind", ["MET", "HB", "OR"])
+def test_served_requests_match_oracle_layer_by_layer(hsg, kind):
+    """Small requests (L <= 16) of one sweep each, of one update kind,
+    arriving faster than they are served, with memory for three of the
+    largest at a time (so that they queue, share ticks and are admitted into
+    freed memory): every request's final spins on every site, layer by
+    layer, against the oracle's half-sweeps from the request's initial state
+    with its own key and temperature, and its E/N against the oracle's
+    energy of its final state.  The oracle is fed the initial spins and
+    device-generated couplings of the request's key as a lone context holds
+    them -- the same generator kernels as the pool's -- after they are
+    checked against the oracle's own Philox maps (1e-6, 1 ulp)."""
+    kw, upd = {
+        "MET": (dict(kind=hsg.HSG_METROPOLIS, hits=4, proposal=hsg.HSG_PROP_BALL, step=0.5), oracle.MET),
+        "HB": (dict(kind=hsg.HSG_HEATBATH), oracle.HB),
+        "OR": (dict(kind=hsg.HSG_NONE, n_or=1), oracle.OR),
+    }[kind]
+    reqs = serve.poisson_trace(12, rate_per_s=20000.0, seed=40 + len(kind), sides=(4, 6, 8, 12, 16),
+                               sweep_range=(1, 1))
+    budget = 3 * 28 * 16 ** 3
+    res, st = serve.serve(reqs, kw, budget, 6, torch.cuda.Stream(), tick_sweeps=1, keep_spins=True, autotune=False)
+    assert st.completed == len(reqs) and st.max_batch >= 2
+    by_id = {q.rid: q for q in reqs}
+    for r in res:
+        q = by_id[r.rid]
+        with hsg.Lattice(q.L, q.seed, q.sample, 0) as lat:
+            lat.generate_couplings()
+            s0, J = lat.spins(), lat.couplings()
+        assert np.max(np.abs(s0 - oracle.init_spins(q.L, q.seed, q.sample, 0))) < 1e-6
+        np.testing.assert_array_max_ulp(J, oracle.gaussian_couplings(q.L, q.seed, q.sample).astype(np.float32),
+                                        maxulp=1)
+        Jd = J.astype(np.float64)
+        label = f"served {kind} L={q.L} T={q.T:.3f} request {q.rid}"
+        if upd == oracle.OR:
+            check_or_sweep(q.L, Jd, s0, r.spins, label=label)
+        else:
+            p = oracle.Params(key=oracle.key(q.seed, q.sample), sweep=0, beta=1.0 / q.T, step=0.5,
+                              hits=kw.get("hits", 1), proposal=hsg.HSG_PROP_BALL)
+            check_one_sweep(q.L, Jd, s0, r.spins, upd, p, label=label)
+        e_ref = oracle.energy(q.L, Jd, r.spins.astype(np.float64)) / q.L ** 3
+        record(label=f"{label} E/N", max_err=abs(r.energy - e_ref))
+        assert abs(r.energy - e_ref) <= 2e-6 and math.isfinite(r.energy)

@@ -20,8 +20,7 @@ pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
 from paper_1006_2566_gb300 import inputs  # noqa: E402
-
-TOL = 1e-5
+from parity_rules import check_or_sweep  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -128,11 +127,13 @@ def test_wave_state_follows_the_current_buffer(hsg):
         assert np.array_equal(x, y)
 
 
-def test_wave_over_relaxation_sweep_matches_oracle(hsg):
-    """One wave OR sweep from a random state against two oracle half-sweeps
-    (the tolerance of the global kernel's sweep test: colour 1 sees colour-0
-    values that carry fp32 round-off); energy conserved to round-off."""
-    L = 40
+@pytest.mark.parametrize("L", [24, 40])
+def test_wave_over_relaxation_sweep_matches_oracle(hsg, L):
+    """One wave OR sweep from a random state, every site of both layers
+    under the half-sweep rules: colour 0 against the oracle's half-sweep of
+    the start state, colour 1 against the oracle's half-sweep of the GPU's
+    own new colour 0 (what the kernel's colour-1 stage read from shared
+    memory); energy conserved to round-off."""
     J, s32 = inputs.gaussian_couplings(L, seed=77), inputs.random_spins(L, seed=78, dtype=np.float32)
     Jr = inputs.round_to_f32(J)
     with hsg.Lattice(L, 2) as lat:
@@ -140,14 +141,9 @@ def test_wave_over_relaxation_sweep_matches_oracle(hsg):
         lat.set_spins(s32)
         e0 = lat.energy()
         lat.sweep(hsg.schedule(kind=hsg.HSG_NONE, n_or=1, kernel=hsg.HSG_KERNEL_WAVE), 1)
-        got = lat.spins().astype(np.float64)
+        got = lat.spins()
         e1 = lat.energy()
-    ref = s32.astype(np.float64)
-    oracle.half_sweep(L, Jr, ref, oracle.OR, 0, oracle.Params())
-    oracle.half_sweep(L, Jr, ref, oracle.OR, 1, oracle.Params())
-    err = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
-    assert np.mean(err <= TOL) >= 0.995
-    assert np.max(err) <= 1e-3
+    check_or_sweep(L, Jr, s32, got, label=f"wave OR sweep L={L}")
     assert abs(e1 - e0) <= 2e-6
 
 
