@@ -205,28 +205,49 @@ __device__ __forceinline__ float3 update_site(float3 s, float3 h, uint32_t site,
   }
 }
 
-// Renormalisation s <- s/|s|.  d = |s|^2 - 1 is formed in fp64 from the
-// exact squares of the fp32 components (three FMAs, error ~1e-16).  Spins
-// drift from unit length only by fp32 round-off, so |d| is tiny and
-// 1/sqrt(1+d) - 1 = -d/2 + 3d^2/8 - 5d^3/16 + O(d^4) (binomial series; for
-// |d| < 2^-8 the remainder is below 2^-33) is evaluated in fp32 and applied
-// as s + s*c with one rounding: the result is within a hair of the
-// correctly rounded s/|s|.  Larger |d| takes the fp64 reciprocal square
-// root; a zero spin is left as is.
+// Knuth's two-sum: s + t = a + b exactly (round-to-nearest fp32, no
+// reassociation; the build keeps additions as written).
+__device__ __forceinline__ float two_sum(float a, float b, float& t) {
+  const float s = a + b;
+  const float bv = s - a;
+  t = (a - (s - bv)) + (b - bv);
+  return s;
+}
+
+// Renormalisation s <- s/|s|.  d = |s|^2 - 1 is formed from error-free fp32
+// transformations: each square as p + e exactly (p = x*x rounded, e =
+// fma(x, x, -p)), the three p summed by two-sums into hi + t1 + t2 exactly,
+// and hi - 1 exact by Sterbenz's lemma while hi is within [1/2, 2].  The
+// leftover terms (each below 2^-23) add up with an error below 2^-43, so d
+// carries what an fp64 evaluation of the squares would give, far below the
+// fp32 rounding of the result -- with no fp64 instruction on GB300's thin
+// FP64 pipe.  Spins drift from unit length only by fp32 round-off, so |d| is
+// tiny and 1/sqrt(1+d) - 1 = -d/2 + 3d^2/8 - 5d^3/16 + O(d^4) (binomial
+// series; for |d| < 2^-8 the remainder is below 2^-33) is evaluated in fp32
+// and applied as s + s*c with one rounding: the result is within a hair of
+// the correctly rounded s/|s|.  Larger |d| (a spin set far from unit length,
+// never reached by sweeps) takes the fp64 reciprocal square root of the fp64
+// |s|^2; a zero spin is left as is.
 __device__ __forceinline__ float4 renorm_spin(float4 v) {
-  const double dx = v.x, dy = v.y, dz = v.z;
-  const double d = fma(dx, dx, fma(dy, dy, fma(dz, dz, -1.0)));
-  const float df = (float)d;
+  const float px = v.x * v.x, py = v.y * v.y, pz = v.z * v.z;
+  const float ex = fmaf(v.x, v.x, -px), ey = fmaf(v.y, v.y, -py), ez = fmaf(v.z, v.z, -pz);
+  float t1, t2;
+  const float hi = two_sum(two_sum(px, py, t1), pz, t2);
+  const float df = (hi - 1.0f) + (((ex + ey) + ez) + (t1 + t2));
   if (fabsf(df) < 0x1p-8f) {
     const float c = df * fmaf(df, fmaf(df, -0.3125f, 0.375f), -0.5f);
     v.x = fmaf(v.x, c, v.x);
     v.y = fmaf(v.y, c, v.y);
     v.z = fmaf(v.z, c, v.z);
-  } else if (d > -1.0) {
-    const double r = rsqrt(d + 1.0);
-    v.x = (float)(dx * r);
-    v.y = (float)(dy * r);
-    v.z = (float)(dz * r);
+  } else {
+    const double dx = v.x, dy = v.y, dz = v.z;
+    const double n2 = fma(dx, dx, fma(dy, dy, dz * dz));
+    if (n2 > 0.0) {
+      const double r = rsqrt(n2);
+      v.x = (float)(dx * r);
+      v.y = (float)(dy * r);
+      v.z = (float)(dz * r);
+    }
   }
   return v;
 }
