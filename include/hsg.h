@@ -47,7 +47,7 @@ enum {
   HSG_EINVAL = 1,   /* bad argument or call order */
   HSG_ENOMEM = 2,   /* device or pinned-host allocation failed */
   HSG_ECUDA = 3,    /* a CUDA runtime call failed (message in hsg_last_error) */
-  HSG_ETIMEOUT = 4, /* a bounded device wait gave up */
+  HSG_ETIMEOUT = 4, /* a bounded device wait gave up (see hsg_energy) */
   HSG_EBUSY = 5     /* resource in use */
 };
 
@@ -94,7 +94,12 @@ enum {
    * kept until hsg_destroy; the two buffers alternate.  The main update of a
    * sweep and hsg_half_sweep use the global kernel.  A renormalisation due
    * right after a sweep is done by that sweep's last wave pass, as it
-   * stores (bit-identical to a renormalisation of its own). */
+   * stores (bit-identical to a renormalisation of its own).  From L = 32
+   * the pass also keeps a halo-padded copy of the couplings for its tensor
+   * loads (about 12 N (1 + 4/L)(1 + 8/L) bytes), made by the first hsg_sweep
+   * that needs it when the device has that much free beside 1 GiB, and
+   * rebuilt (one launch) by the first sweep after new couplings; without it
+   * the pass loads the couplings through registers, with the same results. */
   HSG_KERNEL_WAVE = 3
 };
 
@@ -227,7 +232,9 @@ hsg_status hsg_sweep(hsg_ctx* ctx, const hsg_schedule* schedule, int n_sweeps);
  * E/N of the current state (Eq. 1, each bond once, divided by N = L^3):
  * per-site local fields in FP32, dot products and the deterministic
  * two-pass sum in FP64.  Synchronises the stream.
- * Errors: HSG_EINVAL (NULL, couplings not set), HSG_ECUDA.
+ * Errors: HSG_EINVAL (NULL, couplings not set), HSG_ECUDA, HSG_ETIMEOUT (a
+ * temporally blocked sweep queued before gave up a bounded wait -- 0.2 s --
+ * for its couplings' tensor loads; the spins since then are not valid).
  */
 hsg_status hsg_energy(hsg_ctx* ctx, double* e_per_spin);
 
@@ -413,6 +420,17 @@ const char* hsg_pool_last_error(const hsg_pool* pool);
  * fails as if the device were out of memory; k = 0 disables.  Process-wide.
  */
 hsg_status hsg_test_fail_alloc(int k);
+
+/*
+ * Fault injection for tests of the bounded waits: with on != 0, every
+ * temporally blocked sweep launched from now waits for more bytes than each
+ * of its couplings' tensor loads delivers, so that every such wait runs out
+ * (after 0.2 s; nothing hangs, nothing faults), the sweep's spins are not
+ * valid, and the next hsg_energy on the context returns HSG_ETIMEOUT (once).
+ * on = 0 restores.  Process-wide; a sweep captured in a CUDA graph keeps the
+ * setting it was captured with.  Library-specific.
+ */
+hsg_status hsg_test_stall_tensor_loads(int on);
 
 /*
  * E/N of a lattice held in the caller's own device memory, without any

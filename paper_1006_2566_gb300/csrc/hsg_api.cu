@@ -4,6 +4,7 @@
 // schedule (which kernels run in which order), the energy log and the
 // event-based profiler.  Every step of the Monte Carlo itself runs in the
 // kernels of hsg_sweep.cu and hsg_aux.cu.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -26,6 +27,7 @@ constexpr long long kMaxGraphPeriod = 64;  // longest sweep period captured as o
 
 thread_local std::string g_thread_error;
 int g_fail_alloc_countdown = 0;  // test hook: k-th allocation from now fails
+std::atomic<int> g_test_stall_boxes{0};  // test hook: hsg_test_stall_tensor_loads
 
 // A run of consecutive launches of one kernel class, bracketed by one pair
 // of events (count = launches in the run).
@@ -50,6 +52,13 @@ struct hsg_ctx {
   float4* spins_alt = nullptr;  // [2][Nh], target of the temporally blocked sweeps (allocated on first use)
   float* J = nullptr;       // [3][2][Nh]
   bool have_J = false;
+  // Halo-padded copy of J for the temporally blocked sweep's tensor boxes
+  // (allocated with its tensor map by the first such sweep at L >= 32 when
+  // the device has room for it; rebuilt after every change of J).
+  float* Jpad = nullptr;
+  bool Jpad_ok = false;  // Jpad holds the current J
+  bool use_tma = false;  // bond_map describes Jpad
+  CUtensorMap bond_map{};
   uint64_t sweep = 0;
   void* stage = nullptr;  // site-major staging for host copies
   size_t stage_bytes = 0;
@@ -57,7 +66,7 @@ struct hsg_ctx {
   double* e_out = nullptr;     // hsg_energy result
   double* elog = nullptr;      // energy log
   int elog_cap = 0, elog_n = 0;
-  double* host_e = nullptr;  // pinned, 1 double
+  double* host_e = nullptr;  // pinned, 2 doubles: E/N and the bond-box wait flag
   bool prof = false;
   bool group = false;     // inside hsg_sweep: one event pair per run of same-class launches
   bool run_open = false;  // recs.back() still lacks its stop event
@@ -65,7 +74,8 @@ struct hsg_ctx {
   std::vector<cudaEvent_t> free_events;
   uint64_t launches = 0;
   // Device counters: [0] the sweep counter the kernels read, [1] the energy
-  // log position; the host mirrors both (sweep, elog_n).
+  // log position; the host mirrors both (sweep, elog_n).  [2] is set by a
+  // temporally blocked sweep whose bounded wait for a bond box gave up.
   unsigned long long* d_ctr = nullptr;
   // One captured period of sweeps (see hsg_sweep), replayed while the
   // schedule, the kernel variant and the energy log buffer stay the same.
@@ -178,6 +188,7 @@ void release(hsg_ctx* c) {
   dev_free(c->spins, s);
   dev_free(c->spins_alt, s);
   dev_free(c->J, s);
+  dev_free(c->Jpad, s);
   dev_free(c->stage, s);
   dev_free(c->partials, s);
   dev_free(c->e_out, s);
@@ -296,10 +307,66 @@ hsg_status run_or_sweep_wave(hsg_ctx* c, bool renorm) {
   a.L = c->L;
   a.Lh = c->Lh;
   a.renorm = renorm;
+  a.bond_map = c->use_tma ? &c->bond_map : nullptr;
+  a.err = c->d_ctr + 2;
+  a.box_extra_tx = g_test_stall_boxes.load() ? 16u : 0u;
   hsg_status st = launch(c, renorm ? HSG_PROF_OVERRELAX_RENORM : HSG_PROF_OVERRELAX, 1, "over-relaxation sweep kernel",
                          [&] { return hsg::launch_or_sweep_wave(a, c->sm_count, c->stream); });
   if (st == HSG_OK) std::swap(c->spins, c->spins_alt);
   return st;
+}
+
+// The temporally blocked sweep's tensor-box bonds: at L >= 32, the first
+// sweep allocates the halo-padded copy of J (when the device has room for
+// it beside a margin of 1 GiB; else the sweep keeps its register loads) and
+// encodes its tensor map; a copy older than J is rebuilt (one launch).
+hsg_status prepare_bond_boxes(hsg_ctx* c) {
+  if (c->L < hsg::kWaveTmaMinL || c->packed) return HSG_OK;
+  if (!c->Jpad) {
+    const size_t bytes = sizeof(float) * hsg::padded_bonds_elems(c->L);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess || free_b < bytes + ((size_t)1 << 30)) {
+      cudaGetLastError();
+      return HSG_OK;  // no room: register loads
+    }
+    cudaError_t e = dev_alloc(reinterpret_cast<void**>(&c->Jpad), bytes, c->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      c->Jpad = nullptr;
+      return e == cudaErrorMemoryAllocation ? HSG_OK : cuda_fail(c, e, "padded couplings");
+    }
+    c->Jpad_ok = false;
+    c->use_tma = hsg::encode_padded_bond_map(&c->bond_map, c->Jpad, c->L) == cudaSuccess;
+  }
+  if (c->use_tma && !c->Jpad_ok) {
+    hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling padding kernel",
+                           [&] { return hsg::launch_pad_bonds(c->J, c->Jpad, c->L, c->stream); });
+    if (st != HSG_OK) return st;
+    c->Jpad_ok = true;
+  }
+  return HSG_OK;
+}
+
+// The bond-box wait flag of the temporally blocked sweeps: queue its copy
+// into the second pinned word (after the work queued so far), and, once the
+// stream has been synchronised, HSG_ETIMEOUT if one of them gave up.
+cudaError_t queue_box_flag(hsg_ctx* c) {
+  if (!c->use_tma) return cudaSuccess;
+  return cudaMemcpyAsync(c->host_e + 1, c->d_ctr + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+}
+hsg_status check_box_waits(hsg_ctx* c) {
+  if (!c->use_tma) return HSG_OK;
+  unsigned long long flag = 0;
+  std::memcpy(&flag, c->host_e + 1, sizeof(flag));
+  if (!flag) return HSG_OK;
+  // Reported once: the flag is cleared for the sweeps that follow.
+  cudaError_t e = cudaMemsetAsync(c->d_ctr + 2, 0, sizeof(unsigned long long), c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "wait flag reset");
+  c->host_e[1] = 0.0;
+  return fail(c, HSG_ETIMEOUT,
+              "an over-relaxation sweep gave up waiting for its couplings (bounded wait): the spins since are not "
+              "valid");
 }
 
 // E/N into *out_dev, or (logged) into the energy log at the device position.
@@ -470,7 +537,7 @@ hsg_status hsg_create_layout(hsg_ctx** out, int L, uint64_t seed, uint32_t sampl
       {reinterpret_cast<void**>(&c->J), sizeof(float) * 3 * (size_t)c->N, "couplings"},
       {reinterpret_cast<void**>(&c->partials), sizeof(double) * hsg::energy_partials(L), "energy partials"},
       {reinterpret_cast<void**>(&c->e_out), sizeof(double), "energy result"},
-      {reinterpret_cast<void**>(&c->d_ctr), 2 * sizeof(unsigned long long), "device counters"},
+      {reinterpret_cast<void**>(&c->d_ctr), 3 * sizeof(unsigned long long), "device counters"},
   };
   for (auto& a : allocs) {
     e = dev_alloc(a.p, a.bytes, c->stream);
@@ -486,8 +553,8 @@ hsg_status hsg_create_layout(hsg_ctx** out, int L, uint64_t seed, uint32_t sampl
     release(c);
     return st;
   }
-  e = cudaMallocHost(&c->host_e, sizeof(double));
-  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(unsigned long long), c->stream);
+  e = cudaMallocHost(&c->host_e, 2 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_ctr, 0, 3 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) {
     if (!c->host_e) c->host_e = nullptr;
     st = cuda_fail(nullptr, e, "pinned host slot / counters");
@@ -536,6 +603,7 @@ hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
     if (e != cudaSuccess) return cuda_fail(c, e, "coupling upload sync");
   }
   c->have_J = true;
+  c->Jpad_ok = false;  // the padded copy, if any, is rebuilt before the next sweep
   return HSG_OK;
 }
 
@@ -547,7 +615,10 @@ hsg_status hsg_generate_couplings(hsg_ctx* c) {
   const uint32_t k1 = (uint32_t)(c->seed >> 32) ^ ((2u * c->sample) * 0x9E3779B9u);
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling generator kernel",
                          [&] { return hsg::launch_gen_couplings(c->J, c->L, c->k0, k1, c->stream); });
-  if (st == HSG_OK) c->have_J = true;
+  if (st == HSG_OK) {
+    c->have_J = true;
+    c->Jpad_ok = false;
+  }
   return st;
 }
 
@@ -596,6 +667,7 @@ hsg_status hsg_sweep(hsg_ctx* c, const hsg_schedule* s, int n_sweeps) {
     cudaError_t e = dev_alloc(reinterpret_cast<void**>(&c->spins_alt), sizeof(float4) * (size_t)c->N, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "second spin buffer");
   }
+  if (swaps > 0 && (st = prepare_bond_boxes(c)) != HSG_OK) return st;
   SweepGroup group_guard(c);
   // Sweeps run in periods of P = lcm(renorm_every, energy_every) sweeps
   // (1 without cadences).  On a non-default stream and without the
@@ -638,10 +710,11 @@ hsg_status hsg_energy(hsg_ctx* c, double* e_per_spin) {
   hsg_status st = run_energy(c, c->e_out, false);
   if (st != HSG_OK) return st;
   cudaError_t e = cudaMemcpyAsync(c->host_e, c->e_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = queue_box_flag(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "energy readback");
   *e_per_spin = *c->host_e;
-  return HSG_OK;
+  return check_box_waits(c);
 }
 
 hsg_status hsg_get_energy_log(hsg_ctx* c, double* out, int max_n, int* n) {
@@ -881,6 +954,11 @@ hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t
   const uint32_t k1 = (uint32_t)(seed >> 32) ^ ((2u * sample + replica) * 0x9E3779B9u);
   cudaError_t e = hsg::launch_philox(k0, k1, c1, c2, c3, n, out, static_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return cuda_fail(nullptr, e, "philox kernel");
+  return HSG_OK;
+}
+
+hsg_status hsg_test_stall_tensor_loads(int on) {
+  g_test_stall_boxes.store(on != 0 ? 1 : 0);
   return HSG_OK;
 }
 

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <string>
 
+#include <cuda.h>  // CUtensorMap (the type only; the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 
 namespace hsg {
@@ -102,12 +103,32 @@ struct WaveArgs {
   const float* J;     // J[3][2][N/2]
   int L, Lh;
   bool renorm;  // store every new spin renormalised (renorm_spin)
+  // TMA descriptor of the halo-padded bonds (launch_pad_bonds), or nullptr:
+  // with it the sweep takes each plane's bonds as one tensor box per CTA.
+  const CUtensorMap* bond_map;
+  // Device word that a CTA sets (to 1) when a bounded wait for a tensor
+  // box gave up; the sweep's results are then not to be trusted.
+  unsigned long long* err;
+  // Bytes each box's wait expects beyond the box (0; > 0 only to test the
+  // bounded waits: the waits then cannot complete and run out).
+  uint32_t box_extra_tx;
 };
 
 // Over-relaxation sweep (both colours) in one launch, bit-identical to the
 // colour-0 and colour-1 half-sweeps of launch_half_sweep(U_OR, ...), and
 // with `renorm` set to those half-sweeps followed by launch_renorm.
 cudaError_t launch_or_sweep_wave(const WaveArgs& a, int sm_count, cudaStream_t s);
+
+// Halo-padded copy of the colour-split bonds, read by the sweep's tensor
+// boxes: Jp[a][z][yp][xp] with a = 2d + c, yp = y + 2 in [0, L + 4) and
+// xp = xh + 2 in [0, W), W = roundup(L/2 + 4, 4), holding the bond of
+// (y mod L, xh mod L/2) -- the periodic images of the lattice's edges --
+// so that no box ever wraps.  Used for L >= kWaveTmaMinL.
+constexpr int kWaveTmaMinL = 32;
+size_t padded_bonds_elems(int L);
+cudaError_t launch_pad_bonds(const float* J, float* Jp, int L, cudaStream_t s);
+// The tensor map of Jp (4-D: xp, yp, z, a; box 24 x 17 x 1 x 6 floats).
+cudaError_t encode_padded_bond_map(CUtensorMap* map, const float* Jp, int L);
 
 // Spin layouts (hsg_device.cuh): `packed` = three fp32 component arrays per
 // colour (12 bytes a spin), else float4 per spin.

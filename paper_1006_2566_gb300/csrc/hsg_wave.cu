@@ -32,13 +32,29 @@
 // buffer to another.  The result equals colour 0 then colour 1 of
 // launch_half_sweep exactly.
 //
+// Bonds: from L = 32 (and when the device has room for it) each plane's
+// bonds come as ONE tensor box per CTA (TMA, cp.async.bulk.tensor) from a
+// halo-padded copy of the couplings whose rows and columns carry the
+// periodic images of the lattice's edges, so that no box wraps; the boxes
+// land in a ring of shared-memory slots two planes ahead of their use and
+// complete on mbarriers, with bounded waits.  The bond loads then leave the
+// SM's load/store pipe and its registers, and the colour-1 planes and old
+// spins run two planes ahead as well: 148 us against 155 us per sweep at
+// L = 256, bit-identical.  Smaller lattices load each site's bonds into
+// registers a step ahead (the kernel's other instantiation).
+//
 // Shape (measured on GB300 at L = 256): 16 x 14 tiles make R0 exactly nine
-// warps; 51 KB of shared memory per CTA, three CTAs per SM, and the rest of
-// the SM's unified L1/shared array left to L1 (launch_wave).  Bringing the
-// colour-1 planes in by TMA instead of per-thread cp.async was slower: one
-// 3-D tensor box per plane 165 us, bulk row copies 231 us, against 155 us.
+// warps; three CTAs per SM (51 KB of shared memory each with register
+// bonds, the rest of the SM's unified array left to L1 for their loads;
+// 71 KB with tensor-box bonds).  Bringing the colour-1 planes in by TMA
+// instead of per-thread cp.async was slower: one 3-D tensor box per plane
+// 165 us, bulk row copies 231 us, against 155 us (register bonds).
 // The heat-bath is not blocked this way: recomputing the halo's Philox draws
 // and transcendentals made it compute-bound and slower than two half-sweeps.
+#include <cstddef>
+#include <mutex>
+#include <type_traits>
+
 #include "hsg_device.cuh"
 #include "hsg_internal.h"
 
@@ -52,7 +68,23 @@ constexpr int R0X = WX + 2, R0Y = WY + 2;  // colour-0 region: halo 1
 constexpr int R0N = R0X * R0Y;             // 288
 constexpr int W_THREADS = R0N;             // nine warps
 constexpr int W_MIN_BLOCKS = 3;            // resident CTAs per SM (at most 72 registers)
-constexpr int NS1 = 4, NS0 = 3;            // ring slots
+// Pipeline shape of the two bond paths (measured at L = 256, OR sweep; all
+// bit-identical): C1_LEAD colour-1 planes in flight beyond the three stage 0
+// reads, the old colour-0 spins of stage 0 loaded into registers SL steps
+// ahead, NS0 colour-0 ring slots (two suffice: stage 1 reads planes s and
+// s + 1 and carries s - 1), and with tensor-box bonds BOX_LEAD boxes in
+// flight beyond the two in use.  Register bonds (which stage 0 also loads
+// SL = 1 step ahead): C1_LEAD 1, NS0 3 -- 155 us; C1_LEAD 2 185 us, NS0 2
+// 174 us.  Tensor-box bonds: everything two ahead and NS0 2 -- 148 us;
+// one ahead 154.5 us; 154-161 us for the mixed depths.
+template <bool TMA>
+struct WaveShape {
+  static constexpr int C1_LEAD = TMA ? 2 : 1;
+  static constexpr int SL = TMA ? 2 : 1;
+  static constexpr int NS0 = TMA ? 2 : 3;
+  static constexpr int NS1 = 3 + C1_LEAD;
+};
+constexpr int BOX_LEAD = 2;
 constexpr int MIN_ZC = 8;                  // shortest z chunk
 static_assert(W_THREADS % 32 == 0 && WX * WY <= W_THREADS && R1N <= 2 * W_THREADS, "thread roles");
 
@@ -60,11 +92,35 @@ static_assert(W_THREADS % 32 == 0 && WX * WY <= W_THREADS && R1N <= 2 * W_THREAD
 enum { B_XP = 0, B_YP = 1, B_ZP = 2, B_XM = 3, B_YM = 4, B_ZM = 5, NB = 6 };
 
 struct WaveSmem {
-  float4 c1[NS1][R1N];  // old colour 1 over R1
-  float4 c0[NS0][R0N];  // new colour 0 over R0
+  float4 c1[WaveShape<false>::NS1][R1N];  // old colour 1 over R1
+  float4 c0[WaveShape<false>::NS0][R0N];  // new colour 0 over R0
   float jb[2][NB][R0N];  // bonds of the R0 sites of two planes
 };  // 51,264 bytes
-constexpr size_t W_SMEM = sizeof(WaveSmem);
+
+// Tensor-box bonds: one box per plane holds all six bond arrays
+// (a = 2d + c) of the rows y0 - 2 .. y0 + 14 and the columns xh0 - 2 ..
+// xh0 + 17 of the halo-padded copy -- every bond any site of the CTA's
+// two stages needs on that plane.  Box element (a, row k, col m) is the bond
+// of (y0 - 2 + k, xh0 - 2 + m).  A ring of three planes (s, s + 1 in use,
+// s + 2 .. s + 1 + BOX_LEAD in flight), each slot rounded up to 128 bytes.
+constexpr int TB_X = 20, TB_Y = 17, TB_A = 6;
+constexpr int TB_ARRAY = TB_X * TB_Y;                      // 340 floats
+constexpr uint32_t TB_BYTES = TB_A * TB_ARRAY * 4;         // 8160
+constexpr int TB_SLOT = (TB_BYTES + 127) / 128 * 128 / 4;  // 2048 floats
+constexpr int NTB = 2 + BOX_LEAD;
+constexpr int PAD_X = 2, PAD_Y = 2;  // halo columns / rows of the padded copy on the low side
+struct WaveTmaSmem {
+  float4 c1[WaveShape<true>::NS1][R1N];
+  float4 c0[WaveShape<true>::NS0][R0N];
+  float tb[NTB][TB_SLOT];
+  unsigned long long bar[NTB];  // one mbarrier per ring slot
+};  // 70,816 bytes
+static_assert(offsetof(WaveTmaSmem, tb) % 128 == 0 && offsetof(WaveTmaSmem, bar) % 8 == 0, "slot alignment");
+
+template <bool TMA>
+constexpr size_t wave_smem() {
+  return TMA ? sizeof(WaveTmaSmem) : sizeof(WaveSmem);
+}
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
@@ -73,6 +129,55 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Wait until at most N of this thread's cp.async groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+  return t;
+}
+// Wait until phase `parity` of the mbarrier has completed, for at most
+// about `limit_ns` (and 2^22 polls): false if it gave up.
+__device__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t i = 1; i < (1u << 22); ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 63u) == 0 && global_ns() - t0 > limit_ns) return false;
+  }
+  return false;
+}
+// One tensor box of `map` at coordinates (x, y, z, a) into shared memory,
+// completing on `bar` (its transaction count must expect the box's bytes).
+__device__ __forceinline__ void tma_box_4d(void* dst, const CUtensorMap* map, int x, int y, int z, int a,
+                                           unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(a), "r"(smem_addr(bar))
+      : "memory");
+}
+constexpr unsigned long long kBoxWaitNs = 200000000ull;  // 0.2 s
 
 // v mod n for v >= -2n (region coordinates never go further below 0).
 __device__ __forceinline__ int wrap_mod(int v, int n) { return (v + 2 * n) % n; }
@@ -130,10 +235,20 @@ __device__ __forceinline__ SiteBonds load_bonds(const float* __restrict__ jc, co
 // renormalisation pass right after the sweep; the colour-0 values that
 // stage 1 reads from shared memory are the unrenormalised ones, as in the
 // unfused order.
-template <bool RENORM>
-__global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const WaveArgs a, int zc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  WaveSmem& sm = *reinterpret_cast<WaveSmem*>(smem_raw);
+// TMA: each plane's bonds come as one tensor box of the halo-padded copy
+// (bond_map) into a ring of three shared-memory slots, issued by thread 0
+// two planes ahead and completing on one mbarrier per slot; stage 0 and
+// stage 1 read their bonds there.  Otherwise stage 0 loads its bonds into
+// registers a step ahead and leaves them in shared memory for stage 1.
+// Both read the same bond values, so the results are the same bit for bit.
+template <bool RENORM, bool TMA>
+__global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
+    k_or_sweep_wave(const WaveArgs a, int zc, const __grid_constant__ CUtensorMap bond_map) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  using Smem = std::conditional_t<TMA, WaveTmaSmem, WaveSmem>;
+  constexpr int C1_LEAD = WaveShape<TMA>::C1_LEAD, SL = WaveShape<TMA>::SL;
+  constexpr int NS0 = WaveShape<TMA>::NS0, NS1 = WaveShape<TMA>::NS1;
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   float4(*c1s)[R1N] = sm.c1;
   float4(*c0s)[R0N] = sm.c0;
 
@@ -179,9 +294,13 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
   const uint32_t off1 = y_1 * Lhu + xh_1;
   const int b0 = (r1 + 1) * R0X + (cc1 + 1);    // in R0 coordinates (valid1 only)
   const int own1 = (r1 + 2) * R1X + (cc1 + 2);  // in R1 coordinates (valid1 only)
+  // Box positions of the two sites (TMA): row y - (y0 - 2), column xh - (xh0 - 2).
+  const int tb0 = (r0 + 1) * TB_X + (cc0 + 1);
+  const int tb1 = (r1 + 2) * TB_X + (cc1 + 2);
 
   // Planes are numbered j = 0, 1, ... from z0 - 2; the colour-1 tile of
-  // plane j sits in c1 slot j % NS1, the new colour-0 tile in c0 slot j % NS0.
+  // plane j sits in c1 slot j % NS1, the new colour-0 tile in c0 slot j % NS0
+  // and (TMA) its bond box in tb slot j % NTB.
   // z_of(zs, k): the plane k after plane zs, wrapped (k <= 3 < L).
   auto z_of = [&](uint32_t zs, uint32_t k) { return zs + k >= Lu ? zs + k - Lu : zs + k; };
   auto z_below = [&](uint32_t z) { return z == 0 ? Lu - 1 : z - 1; };
@@ -191,38 +310,93 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
     cp_async16(&slot[t], src1 + zo + l1_off[0]);
     if (l1_second) cp_async16(&slot[t + W_THREADS], src1 + zo + l1_off[1]);
   };
-  // Register inputs of stage 0 on plane z: its bonds and old spin.
+  // Register inputs of stage 0 on plane z: its bonds (unless they come by
+  // tensor box) and old spin.
   auto load0 = [&](uint32_t z, SiteBonds& b, float3& s) {
     const uint32_t zo = z * plane;
-    b = load_bonds(j0, j1, Nh2, o0, (y_0 + z) & 1u, zo, z_below(z) * plane);
+    if constexpr (!TMA) b = load_bonds(j0, j1, Nh2, o0, (y_0 + z) & 1u, zo, z_below(z) * plane);
     const float4 v = ld_early4(src0 + zo + o0.off);
     s = make_float3(v.x, v.y, v.z);
   };
 
+  // Tensor boxes (TMA): thread 0 issues the box of plane j; every thread
+  // waits for it before reading it.  A wait that gives up marks the
+  // sweep as failed (a.err), stops further boxes and waits, and lets the
+  // CTA run to its end; thread 0 then waits, again bounded, for the boxes
+  // still in flight, so that none lands after the CTA has exited.
+  bool box_ok = true;
+  int boxes_issued = 0, boxes_seen = 0;
+  auto issue_box = [&](int j, uint32_t z) {
+    if constexpr (TMA) {
+      const int k = j % NTB;
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of the slot, then the box
+      mbar_expect_tx(&sm.bar[k], TB_BYTES + a.box_extra_tx);
+      tma_box_4d(sm.tb[k], &bond_map, xh0, y0, (int)z, 0, &sm.bar[k]);
+      boxes_issued = j + 1;
+    }
+  };
+  auto wait_box = [&](int j) {
+    if constexpr (TMA) {
+      if (!box_ok) return;
+      if (mbar_wait_bounded(&sm.bar[j % NTB], (uint32_t)(j / NTB) & 1u, kBoxWaitNs)) {
+        boxes_seen = j + 1;
+      } else {
+        box_ok = false;
+        atomicOr(a.err, 1ull);
+      }
+    }
+  };
+
   SiteBonds cb0{}, nb0{};
   float jzm1 = 0.0f;  // stage 1: the -z bond of this column, from the plane before
-  float3 cs0 = make_float3(0.0f, 0.0f, 0.0f), ns0 = cs0;
+  float3 cs0 = make_float3(0.0f, 0.0f, 0.0f), ns0 = cs0, n2s0 = cs0;  // stage 0's old spins, planes s + 1 ..
   // Column carries: stage 0's old colour 1 on planes s, s + 1 (a0, a1),
   // stage 1's new colour 0 on planes s - 1, s (bm, bc).
   float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0, bm = a0, bc = a0;
   uint32_t zs = (uint32_t)wrap_mod(z0 - 2, L);  // plane of j = s
+  if constexpr (TMA) {
+    if (t == 0) {
+#pragma unroll
+      for (int k = 0; k < NTB; ++k) mbar_init(&sm.bar[k], 1);
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (t == 0)
+#pragma unroll
+      for (int j = 0; j <= BOX_LEAD; ++j) issue_box(j, z_of(zs, j));
+  }
   load_c1(0, zs);
   load_c1(1, z_of(zs, 1));
   load_c1(2, z_of(zs, 2));
   cp_async_commit();
+#pragma unroll
+  for (int k = 1; k < C1_LEAD; ++k) {  // one group per plane beyond
+    load_c1(2 + k, z_of(zs, 2 + k));
+    cp_async_commit();
+  }
   load0(z_of(zs, 1), cb0, cs0);
+  if constexpr (SL == 2) load0(z_of(zs, 2), nb0, ns0);
+  wait_box(0);
 
   for (int s = 0; s < nsteps; ++s) {
-    // Ring slots of planes s .. s + 3 (colour 1) and s - 1 .. s + 1 (colour 0).
-    const int k0 = s % NS1, k1 = (s + 1) % NS1, k2 = (s + 2) % NS1, k3 = (s + 3) % NS1;
+    // Ring slots of planes s .. s + 2 (colour 1) and s, s + 1 (colour 0).
+    const int k0 = s % NS1, k1 = (s + 1) % NS1, k2 = (s + 2) % NS1;
     const int c00 = s % NS0, c0p = (s + 1) % NS0;
-    const uint32_t z1p = z_of(zs, 1), z2p = z_of(zs, 2), z3p = z_of(zs, 3);
-    asm volatile("cp.async.wait_all;\n" ::: "memory");  // colour-1 planes up to s + 2
-    __syncthreads();  // ... visible to all; step s-1 is done with the slot refilled next
-    if (s + 3 <= nsteps + 1) load_c1(k3, z3p);
+    const uint32_t z1p = z_of(zs, 1), z2p = z_of(zs, 2);
+    cp_async_wait<C1_LEAD - 1>();  // colour-1 planes up to s + 2
+    __syncthreads();  // ... visible to all; step s-1 is done with the slots refilled next
+    if (s + 2 + C1_LEAD <= nsteps + 1) load_c1((s + 2 + C1_LEAD) % NS1, z_of(zs, 2 + C1_LEAD));
     cp_async_commit();
-    // Next step's register inputs of stage 0 (plane s + 2).
-    if (s + 1 < nsteps) load0(z2p, nb0, ns0);
+    // TMA: the box of plane s + 1 + BOX_LEAD into the slot of plane s - 1
+    // (done with at step s - 1), and the wait for plane s + 1, stage 0's.
+    if (t == 0 && box_ok && s + 1 + BOX_LEAD <= nsteps) issue_box(s + 1 + BOX_LEAD, z_of(zs, 1 + BOX_LEAD));
+    wait_box(s + 1);
+    // Register inputs of stage 0, SL steps ahead.
+    if constexpr (SL == 2) {
+      if (s + 2 < nsteps) load0(z_of(zs, 3), nb0, n2s0);
+    } else {
+      if (s + 1 < nsteps) load0(z2p, nb0, ns0);
+    }
 
     // Stage 0: colour 0 on plane j = s + 1 (stored when s in [1, z1 - z0]).
     // Its -z, +z and one of its x neighbours sit in its own column on
@@ -247,25 +421,40 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
       in.szm = a0;
       a0 = a1;
       a1 = a2;
-      in.jxp = cb0.xp;
-      in.jxm = cb0.xm;
-      in.jyp = cb0.yp;
-      in.jym = cb0.ym;
-      in.jzp = cb0.zp;
-      in.jzm = cb0.zm;
+      if constexpr (TMA) {
+        // Its +d bonds and the -x / -y bonds (the +x / +y bonds of its -x /
+        // -y neighbours, colour 1) on plane s + 1; the -z bond (the +z bond
+        // of the colour-1 site below) on plane s.
+        const float* B = sm.tb[(s + 1) % NTB];
+        in.jxp = B[0 * TB_ARRAY + tb0];
+        in.jxm = B[1 * TB_ARRAY + tb0 - (p ? 0 : 1)];
+        in.jyp = B[2 * TB_ARRAY + tb0];
+        in.jym = B[3 * TB_ARRAY + tb0 - TB_X];
+        in.jzp = B[4 * TB_ARRAY + tb0];
+        in.jzm = sm.tb[s % NTB][5 * TB_ARRAY + tb0];
+      } else {
+        in.jxp = cb0.xp;
+        in.jxm = cb0.xm;
+        in.jyp = cb0.yp;
+        in.jym = cb0.ym;
+        in.jzp = cb0.zp;
+        in.jzm = cb0.zm;
+      }
       in.s = cs0;
       in.q = 0;
       in.site = 0;  // over-relaxation draws no random numbers
       const float4 v = site_result<U_OR>(in, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
       c0s[c0p][t] = v;
       if (owned0 && s >= 1 && s <= z1 - z0) dst0[z * plane + o0.off] = RENORM ? renorm_spin(v) : v;
-      float(*jb)[R0N] = sm.jb[(s + 1) & 1];
-      jb[B_XP][t] = cb0.xp;
-      jb[B_YP][t] = cb0.yp;
-      jb[B_ZP][t] = cb0.zp;
-      jb[B_XM][t] = cb0.xm;
-      jb[B_YM][t] = cb0.ym;
-      jb[B_ZM][t] = cb0.zm;
+      if constexpr (!TMA) {
+        float(*jb)[R0N] = sm.jb[(s + 1) & 1];
+        jb[B_XP][t] = cb0.xp;
+        jb[B_YP][t] = cb0.yp;
+        jb[B_ZP][t] = cb0.zp;
+        jb[B_XM][t] = cb0.xm;
+        jb[B_YM][t] = cb0.ym;
+        jb[B_ZM][t] = cb0.zm;
+      }
     }
     __syncthreads();
 
@@ -276,7 +465,6 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
     // -z = the +z bond of the site below (kept from the step before).
     // Its own column of new colour 0 on planes s - 1, s, s + 1 likewise:
     // plane s + 1 (just written by stage 0) is loaded, the others carried.
-    const float(*jb)[R0N] = sm.jb[s & 1];
     const float4 b2 = valid1 ? c0s[c0p][b0] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     if (s >= 2 && valid1) {
       const uint32_t z = zs;
@@ -290,11 +478,23 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
       in.sym = n0[-R0X];
       in.szp = b2;
       in.szm = bm;
-      in.jxp = jb[B_XM][b0 + (int)p];
-      in.jxm = jb[B_XP][b0 - 1 + (int)p];
-      in.jyp = jb[B_YM][b0 + R0X];
-      in.jym = jb[B_YP][b0 - R0X];
-      in.jzp = sm.jb[(s + 1) & 1][B_ZM][b0];
+      if constexpr (TMA) {
+        // Plane s's box: its own +d bonds (colour 1) and the +x / +y bonds
+        // of its -x / -y neighbours (colour 0); -z carried.
+        const float* B = sm.tb[s % NTB];
+        in.jxp = B[1 * TB_ARRAY + tb1];
+        in.jxm = B[0 * TB_ARRAY + tb1 - 1 + (int)p];
+        in.jyp = B[3 * TB_ARRAY + tb1];
+        in.jym = B[2 * TB_ARRAY + tb1 - TB_X];
+        in.jzp = B[5 * TB_ARRAY + tb1];
+      } else {
+        const float(*jb)[R0N] = sm.jb[s & 1];
+        in.jxp = jb[B_XM][b0 + (int)p];
+        in.jxm = jb[B_XP][b0 - 1 + (int)p];
+        in.jyp = jb[B_YM][b0 + R0X];
+        in.jym = jb[B_YP][b0 - R0X];
+        in.jzp = sm.jb[(s + 1) & 1][B_ZM][b0];
+      }
       in.jzm = jzm1;
       const float4 o = c1s[k0][own1];
       in.s = make_float3(o.x, o.y, o.z);
@@ -303,12 +503,25 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
       const float4 r = site_result<U_OR>(in, 1u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
       dst1[z * plane + off1] = RENORM ? renorm_spin(r) : r;
     }
-    if (s >= 1 && valid1) jzm1 = jb[B_ZP][b0];
+    if (s >= 1 && valid1) {
+      if constexpr (TMA)
+        jzm1 = sm.tb[s % NTB][4 * TB_ARRAY + tb1];
+      else
+        jzm1 = sm.jb[s & 1][B_ZP][b0];
+    }
     bm = bc;
     bc = b2;
     cb0 = nb0;
     cs0 = ns0;
+    if constexpr (SL == 2) ns0 = n2s0;
     zs = z1p;
+  }
+  if constexpr (TMA) {
+    // A CTA whose wait gave up: its issuing thread waits (bounded) for the
+    // boxes still in flight before the CTA exits.
+    if (t == 0)
+      for (int j = boxes_seen; j < boxes_issued; ++j)
+        if (!mbar_wait_bounded(&sm.bar[j % NTB], (uint32_t)(j / NTB) & 1u, kBoxWaitNs)) break;
   }
 }
 
@@ -323,29 +536,41 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave(const
 //    one full wave: 166 us; six per SM (two waves) 167 us; two per SM 196 us;
 //    four per SM (a partial second wave) 234 us.
 constexpr int W_CARVEOUT_PCT = 58;
+// With tensor-box bonds stage 0's bond loads no longer pass through L1: the
+// carveout is the smallest that holds three CTAs (each with the 1 KB the
+// system reserves), as a percentage of the 228 KB maximum, which the driver
+// rounds up to a supported configuration (70.8 KB per CTA: 93 % -> 228 KB).
+constexpr int W_TMA_CARVEOUT_PCT = (int)((100 * 3 * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472);
 constexpr int W_GRID_PER_SM = 3;
 
 // The kernel attributes are per device: applied once on each device used.
-template <bool RENORM>
+template <bool RENORM, bool TMA>
 cudaError_t configure_wave() {
   static PerDevice configured;
   cudaError_t e = cudaSuccess;
   std::atomic<int>* slot = device_slot(configured, &e);
   if (!slot) return e;
   if (slot->load(std::memory_order_acquire) == 0) {
-    e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W_SMEM);
+    e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)wave_smem<TMA>());
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               W_CARVEOUT_PCT);
+      e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM, TMA>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               TMA ? W_TMA_CARVEOUT_PCT : W_CARVEOUT_PCT);
     if (e != cudaSuccess) return e;
     slot->store(1, std::memory_order_release);
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
-  const cudaError_t e = a.renorm ? configure_wave<true>() : configure_wave<false>();
+template <bool RENORM, bool TMA>
+cudaError_t launch_wave_as(const WaveArgs& a, dim3 grid, int zc, const CUtensorMap& map, cudaStream_t s) {
+  const cudaError_t e = configure_wave<RENORM, TMA>();
   if (e != cudaSuccess) return e;
+  k_or_sweep_wave<RENORM, TMA><<<grid, W_THREADS, wave_smem<TMA>(), s>>>(a, zc, map);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
   const unsigned tx = cdiv(a.Lh, WX), ty = cdiv(a.L, WY);
   long long chunks = (long long)W_GRID_PER_SM * sm_count / ((long long)tx * ty);
   if (chunks < 1) chunks = 1;
@@ -353,18 +578,95 @@ cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
   if (zc < MIN_ZC) zc = MIN_ZC;
   if (zc > a.L) zc = a.L;
   const dim3 grid(tx, ty, cdiv(a.L, zc));
-  if (a.renorm)
-    k_or_sweep_wave<true><<<grid, W_THREADS, W_SMEM, s>>>(a, zc);
-  else
-    k_or_sweep_wave<false><<<grid, W_THREADS, W_SMEM, s>>>(a, zc);
-  return cudaGetLastError();
+  // The renormalising sweep (one in renorm_every) keeps the register bonds:
+  // with them it measured 165.7 us against 174.7 us with tensor boxes.
+  if (a.bond_map && !a.renorm) return launch_wave_as<false, true>(a, grid, zc, *a.bond_map, s);
+  static const CUtensorMap unused{};
+  return a.renorm ? launch_wave_as<true, false>(a, grid, zc, unused, s)
+                  : launch_wave_as<false, false>(a, grid, zc, unused, s);
+}
+
+// Padded copy (see padded_bonds_elems): width W of its rows.
+inline uint32_t padded_width(int L) { return (uint32_t)((L / 2 + PAD_X + 2 + 3) / 4 * 4); }
+
+// The padded copy, one warp per padded row (a, z, yp) at a time: the row of
+// bond array a at (z, y = yp - 2 mod L), its columns shifted by PAD_X and
+// wrapped.
+__global__ void __launch_bounds__(256) k_pad_bonds(const float* __restrict__ J, float* __restrict__ Jp, int L,
+                                                   int Lh, uint32_t W, uint32_t rows) {
+  const uint32_t H = (uint32_t)L + 2 * PAD_Y;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); row < rows; row += warps) {
+    const uint32_t yp = row % H, za = row / H;
+    const uint32_t z = za % (uint32_t)L, arr = za / (uint32_t)L;
+    int y = (int)yp - PAD_Y;
+    y = y < 0 ? y + L : (y >= L ? y - L : y);
+    const float* __restrict__ src = J + (size_t)arr * ((size_t)L * L * Lh) + ((size_t)z * L + (size_t)y) * Lh;
+    float* __restrict__ dst = Jp + (size_t)row * W;
+    for (uint32_t xp = lane; xp < W; xp += 32) {
+      int xh = (int)xp - PAD_X;
+      while (xh < 0) xh += Lh;
+      while (xh >= Lh) xh -= Lh;
+      dst[xp] = __ldg(src + xh);
+    }
+  }
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once (the library links the
+// CUDA runtime only).
+EncodeTiledFn tensor_map_encoder() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
 }
 
 }  // namespace
 
 cudaError_t launch_or_sweep_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
   if (a.L < 4 || (a.L & 1) || a.src == a.dst) return cudaErrorInvalidValue;
+  if (a.bond_map && (a.L < kWaveTmaMinL || !a.err)) return cudaErrorInvalidValue;
   return launch_wave(a, sm_count, s);
+}
+
+size_t padded_bonds_elems(int L) { return (size_t)6 * L * (L + 2 * PAD_Y) * padded_width(L); }
+
+cudaError_t launch_pad_bonds(const float* J, float* Jp, int L, cudaStream_t s) {
+  if (L < kWaveTmaMinL || (L & 1)) return cudaErrorInvalidValue;
+  const uint32_t rows = (uint32_t)(TB_A * L * (L + 2 * PAD_Y));  // < 2^24 for L <= 1624
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const uint32_t blocks = (uint32_t)sms * 8u < (rows + 7u) / 8u ? (uint32_t)sms * 8u : (rows + 7u) / 8u;
+  k_pad_bonds<<<blocks, 256, 0, s>>>(J, Jp, L, L / 2, padded_width(L), rows);
+  return cudaGetLastError();
+}
+
+cudaError_t encode_padded_bond_map(CUtensorMap* map, const float* Jp, int L) {
+  if (L < kWaveTmaMinL || (L & 1) || (reinterpret_cast<uintptr_t>(Jp) & 15)) return cudaErrorInvalidValue;
+  const EncodeTiledFn encode = tensor_map_encoder();
+  if (!encode) return cudaErrorNotSupported;
+  const cuuint64_t W = padded_width(L), H = (cuuint64_t)L + 2 * PAD_Y;
+  const cuuint64_t dims[4] = {W, H, (cuuint64_t)L, (cuuint64_t)TB_A};
+  const cuuint64_t strides[3] = {W * 4, W * H * 4, W * H * (cuuint64_t)L * 4};
+  const cuuint32_t box[4] = {TB_X, TB_Y, 1, TB_A};
+  const cuuint32_t elem_strides[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(Jp), dims, strides, box,
+                            elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace hsg

@@ -91,6 +91,7 @@ _SIGS = {
     "hsg_version": ([], _i),
     "hsg_philox": ([_u64, _u32, _u32, _u32, _u32, _u32, _u32, _vp, _vp], _i),
     "hsg_test_fail_alloc": ([_i], _i),
+    "hsg_test_stall_tensor_loads": ([_i], _i),
     "hsg_energy_noalloc": ([_i, _vp, _vp, _vp, _vp], _i),
     "hsg_pool_create": ([ctypes.POINTER(_vp), _u64, _i, _vp], _i),
     "hsg_pool_destroy": ([_vp], _i),
@@ -311,6 +312,10 @@ def hsg_philox(seed: int, sample: int, replica: int, c1: int, c2: int, c3: int, 
 
 def hsg_test_fail_alloc(k: int) -> None:
     _check(_lib.hsg_test_fail_alloc(int(k)))
+
+
+def hsg_test_stall_tensor_loads(on: bool) -> None:
+    _check(_lib.hsg_test_stall_tensor_loads(1 if on else 0))
 
 
 def hsg_energy_noalloc(L: int, spins, J, e_out, stream=None) -> None:

@@ -223,3 +223,70 @@ def test_wave_fuses_the_renormalisation_into_the_last_over_relaxation_sweep(hsg)
                               for k in (hsg.HSG_PROF_OVERRELAX, hsg.HSG_PROF_OVERRELAX_RENORM, hsg.HSG_PROF_RENORM)]
     assert counts[hsg.HSG_KERNEL_WAVE] == [6, 2, 0]  # the last OR sweep of sweeps 2 and 4 renormalises
     assert counts[hsg.HSG_KERNEL_GLOBAL] == [16, 0, 2]
+
+
+@pytest.mark.parametrize("source", ["f32", "f64", "generated"])
+def test_new_couplings_after_wave_sweeps(hsg, source):
+    """From L = 32 the temporally blocked sweep reads its bonds from a
+    halo-padded copy of the couplings, made by its first sweep.  New
+    couplings after that -- uploaded (fp32 or fp64) or generated on the
+    device, the copy rebuilt before the next sweep -- must read back exactly
+    and sweep bit for bit as with the global kernel."""
+    L = 40
+    J1 = inputs.gaussian_couplings(L, seed=41, dtype=np.float32)
+    J2 = inputs.gaussian_couplings(L, seed=42)
+    sched = dict(kind=hsg.HSG_HEATBATH, T=0.6, n_or=2, renorm_every=2)
+    outs = []
+    for kernel in (hsg.HSG_KERNEL_GLOBAL, hsg.HSG_KERNEL_WAVE):
+        with hsg.Lattice(L, 9, 3) as lat:
+            lat.set_couplings(J1)
+            lat.sweep(hsg.schedule(kernel=kernel, **sched), 1)
+            if source == "generated":
+                lat.generate_couplings()
+                want_J = oracle.gaussian_couplings(L, 9, 3).astype(np.float32)
+                np.testing.assert_array_max_ulp(lat.couplings(), want_J, maxulp=1)
+            else:
+                lat.set_couplings(J2.astype(np.float32) if source == "f32" else J2)
+                assert np.array_equal(lat.couplings(), J2.astype(np.float32))
+            lat.sweep(hsg.schedule(kernel=kernel, **sched), 2)
+            outs.append((lat.spins(), lat.couplings()))
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][0], outs[1][0])
+
+
+def test_tensor_load_waits_run_out_and_are_reported(hsg):
+    """The waits of the temporally blocked sweep for its couplings' tensor
+    loads are bounded (0.2 s).  With the test switch each wait expects more
+    bytes than its load delivers, so every wait runs out: the sweep still
+    ends, hsg_energy reports HSG_ETIMEOUT (once), and the context stays
+    usable -- with the switch off, the same sweep from the same state equals
+    the global kernel's bit for bit."""
+    import time
+
+    L = 40
+    J = inputs.gaussian_couplings(L, seed=51, dtype=np.float32)
+    sched = hsg.schedule(kind=hsg.HSG_NONE, n_or=1, kernel=hsg.HSG_KERNEL_WAVE)
+    with hsg.Lattice(L, 51) as lat:  # the default stream: launches issued directly, no captured graph
+        lat.set_couplings(J)
+        lat.sweep(sched, 1)  # makes the padded copy: tensor loads from here on
+        lat.energy()
+        s0 = lat.spins()
+        hsg.hsg_test_stall_tensor_loads(True)
+        try:
+            t0 = time.perf_counter()
+            lat.sweep(sched, 1)
+            with pytest.raises(hsg.HsgError) as e:
+                lat.energy()
+            assert e.value.status == hsg.HSG_ETIMEOUT
+            assert time.perf_counter() - t0 < 10.0
+        finally:
+            hsg.hsg_test_stall_tensor_loads(False)
+        lat.energy()  # reported once
+        lat.set_spins(s0)
+        lat.sweep(sched, 1)
+        got = lat.spins()
+    with hsg.Lattice(L, 51) as ref:
+        ref.set_couplings(J)
+        ref.set_spins(s0)
+        ref.sweep(hsg.schedule(kind=hsg.HSG_NONE, n_or=1, kernel=hsg.HSG_KERNEL_GLOBAL), 1)
+        assert np.array_equal(got, ref.spins())
