@@ -97,8 +97,9 @@ enum {
    * stores (bit-identical to a renormalisation of its own).  From L = 32
    * the pass also keeps a halo-padded copy of the couplings for its tensor
    * loads (about 12 N (1 + 4/L)(1 + 8/L) bytes), made by the first hsg_sweep
-   * that needs it when the device has that much free beside 1 GiB, and
-   * rebuilt (one launch) by the first sweep after new couplings; without it
+   * that needs it when the device has that much free beside 1 GiB, written
+   * by hsg_set_couplings from then on, and rebuilt (one launch) by the first
+   * sweep after hsg_generate_couplings; without it
    * the pass loads the couplings through registers, with the same results. */
   HSG_KERNEL_WAVE = 3
 };

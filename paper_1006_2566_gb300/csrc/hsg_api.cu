@@ -594,8 +594,11 @@ hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
     if (e != cudaSuccess) return cuda_fail(c, e, "coupling upload");
     src = c->stage;
   }
+  // With a padded copy in use (temporally blocked sweeps at L >= 32) the
+  // same launch writes it too.
+  float* const Jp = c->use_tma ? c->Jpad : nullptr;
   hsg_status st = launch(c, HSG_PROF_LAYOUT, 1, "coupling layout kernel",
-                         [&] { return hsg::launch_scatter_couplings(src, f64, c->J, c->L, c->stream); });
+                         [&] { return hsg::launch_scatter_couplings(src, f64, c->J, c->L, c->stream, Jp); });
   if (st != HSG_OK) return st;
   if (where == HSG_HOST) {
     // The caller may reuse its array as soon as we return.
@@ -603,7 +606,7 @@ hsg_status hsg_set_couplings(hsg_ctx* c, const void* J, int dtype, int where) {
     if (e != cudaSuccess) return cuda_fail(c, e, "coupling upload sync");
   }
   c->have_J = true;
-  c->Jpad_ok = false;  // the padded copy, if any, is rebuilt before the next sweep
+  c->Jpad_ok = Jp != nullptr;
   return HSG_OK;
 }
 

@@ -61,7 +61,7 @@ __global__ void k_init_spins(void* __restrict__ S, int L, uint32_t k0, uint32_t 
 
 // Site-major -> colour-split couplings.  Thread per site (x, y, z).
 template <typename T>
-__global__ void k_scatter_couplings(const T* __restrict__ src, float* __restrict__ J, int L) {
+__global__ void k_scatter_couplings(const T* __restrict__ src, float* __restrict__ J, int L, float* __restrict__ Jp) {
   const int x = blockIdx.x * 64 + threadIdx.x;
   const int y = blockIdx.y * 4 + threadIdx.y;
   const int z = blockIdx.z;
@@ -71,8 +71,26 @@ __global__ void k_scatter_couplings(const T* __restrict__ src, float* __restrict
   const long long i = (long long)x + (long long)y * L + (long long)z * L * L;
   const int c = (x + y + z) & 1;
   const long long q = ((long long)z * L + y) * Lh + (x >> 1);
+  float v[3];
 #pragma unroll
-  for (int d = 0; d < 3; ++d) J[(2 * d + c) * nh + q] = (float)src[3 * i + d];
+  for (int d = 0; d < 3; ++d) {
+    v[d] = (float)src[3 * i + d];
+    J[(2 * d + c) * nh + q] = v[d];
+  }
+  if (Jp) {
+    // The padded copy holds this bond at (y + 2, xh + 2) and at the
+    // periodic images inside its halo: rows y + 2 +- L, columns xh + 2 +- L/2.
+    const int xh = x >> 1, W = (int)padded_width(L), H = L + 2 * kPadY;
+    const int rows[2] = {y + kPadY, y < kPadY ? y + kPadY + L : (y >= L - kPadY ? y + kPadY - L : -1)};
+    const int cols[2] = {xh + kPadX, xh + kPadX + Lh < W ? xh + kPadX + Lh : (xh >= Lh - kPadX ? xh + kPadX - Lh : -1)};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      float* plane = Jp + ((size_t)(2 * d + c) * L + z) * H * W;
+      for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+          if (rows[a] >= 0 && cols[b] >= 0) plane[(size_t)rows[a] * W + cols[b]] = v[d];
+    }
+  }
 }
 
 // Gaussian couplings from Philox kind JGEN (key of (seed, sample), shared by
@@ -280,12 +298,13 @@ cudaError_t launch_init_spins(void* S, bool packed, int L, uint32_t k0, uint32_t
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s) {
+cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s, float* Jp) {
+  if (Jp && L < kWaveTmaMinL) return cudaErrorInvalidValue;
   const dim3 grid(cdiv(L, 64), cdiv(L, 4), (unsigned)L), block(64, 4);
   if (f64)
-    k_scatter_couplings<double><<<grid, block, 0, s>>>(static_cast<const double*>(src), J, L);
+    k_scatter_couplings<double><<<grid, block, 0, s>>>(static_cast<const double*>(src), J, L, Jp);
   else
-    k_scatter_couplings<float><<<grid, block, 0, s>>>(static_cast<const float*>(src), J, L);
+    k_scatter_couplings<float><<<grid, block, 0, s>>>(static_cast<const float*>(src), J, L, Jp);
   return cudaGetLastError();
 }
 

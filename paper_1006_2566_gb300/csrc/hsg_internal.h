@@ -125,6 +125,10 @@ cudaError_t launch_or_sweep_wave(const WaveArgs& a, int sm_count, cudaStream_t s
 // (y mod L, xh mod L/2) -- the periodic images of the lattice's edges --
 // so that no box ever wraps.  Used for L >= kWaveTmaMinL.
 constexpr int kWaveTmaMinL = 32;
+constexpr int kPadX = 2, kPadY = 2;  // halo columns / rows of the padded copy on the low side
+// Width W of the padded copy's rows: room for xh in [-2, L/2 + 2), rounded
+// up to a multiple of four floats (16-byte rows, as tensor maps want).
+__host__ __device__ inline uint32_t padded_width(int L) { return (uint32_t)((L / 2 + kPadX + 2 + 3) / 4 * 4); }
 size_t padded_bonds_elems(int L);
 cudaError_t launch_pad_bonds(const float* J, float* Jp, int L, cudaStream_t s);
 // The tensor map of Jp (4-D: xp, yp, z, a; box 24 x 17 x 1 x 6 floats).
@@ -135,8 +139,10 @@ cudaError_t encode_padded_bond_map(CUtensorMap* map, const float* Jp, int L);
 // Spin initialisation: S from Philox kind INIT.  One launch.
 cudaError_t launch_init_spins(void* S, bool packed, int L, uint32_t k0, uint32_t k1, cudaStream_t s);
 
-// Site-major -> colour-split couplings (src: 3N fp32 or fp64).  One launch.
-cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s);
+// Site-major -> colour-split couplings (src: 3N fp32 or fp64); with Jp not
+// NULL also its halo-padded copy (launch_pad_bonds' layout), from the same
+// values.  One launch.
+cudaError_t launch_scatter_couplings(const void* src, bool f64, float* J, int L, cudaStream_t s, float* Jp = nullptr);
 
 // Gaussian couplings from Philox kind JGEN under key (k0, k1), written
 // colour-split; and colour-split -> site-major fp32 couplings.  One launch each.

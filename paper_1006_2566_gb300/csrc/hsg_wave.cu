@@ -103,12 +103,13 @@ struct WaveSmem {
 // two stages needs on that plane.  Box element (a, row k, col m) is the bond
 // of (y0 - 2 + k, xh0 - 2 + m).  A ring of three planes (s, s + 1 in use,
 // s + 2 .. s + 1 + BOX_LEAD in flight), each slot rounded up to 128 bytes.
-constexpr int TB_X = 20, TB_Y = 17, TB_A = 6;
+constexpr int TB_X = WX + 4, TB_Y = WY + 3, TB_A = 6;  // 20 x 17 x 6 floats
+static_assert(TB_X % 4 == 0, "a box row is a multiple of 16 bytes");
 constexpr int TB_ARRAY = TB_X * TB_Y;                      // 340 floats
 constexpr uint32_t TB_BYTES = TB_A * TB_ARRAY * 4;         // 8160
 constexpr int TB_SLOT = (TB_BYTES + 127) / 128 * 128 / 4;  // 2048 floats
 constexpr int NTB = 2 + BOX_LEAD;
-constexpr int PAD_X = 2, PAD_Y = 2;  // halo columns / rows of the padded copy on the low side
+constexpr int PAD_X = kPadX, PAD_Y = kPadY;
 struct WaveTmaSmem {
   float4 c1[WaveShape<true>::NS1][R1N];
   float4 c0[WaveShape<true>::NS0][R0N];
@@ -540,7 +541,8 @@ constexpr int W_CARVEOUT_PCT = 58;
 // carveout is the smallest that holds three CTAs (each with the 1 KB the
 // system reserves), as a percentage of the 228 KB maximum, which the driver
 // rounds up to a supported configuration (70.8 KB per CTA: 93 % -> 228 KB).
-constexpr int W_TMA_CARVEOUT_PCT = (int)((100 * 3 * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472);
+constexpr int W_TMA_CARVEOUT_PCT =
+    (int)((100 * W_MIN_BLOCKS * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472);
 constexpr int W_GRID_PER_SM = 3;
 
 // The kernel attributes are per device: applied once on each device used.
@@ -585,9 +587,6 @@ cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
   return a.renorm ? launch_wave_as<true, false>(a, grid, zc, unused, s)
                   : launch_wave_as<false, false>(a, grid, zc, unused, s);
 }
-
-// Padded copy (see padded_bonds_elems): width W of its rows.
-inline uint32_t padded_width(int L) { return (uint32_t)((L / 2 + PAD_X + 2 + 3) / 4 * 4); }
 
 // The padded copy, one warp per padded row (a, z, yp) at a time: the row of
 // bond array a at (z, y = yp - 2 mod L), its columns shifted by PAD_X and

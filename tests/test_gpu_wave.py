@@ -229,9 +229,10 @@ def test_wave_fuses_the_renormalisation_into_the_last_over_relaxation_sweep(hsg)
 def test_new_couplings_after_wave_sweeps(hsg, source):
     """From L = 32 the temporally blocked sweep reads its bonds from a
     halo-padded copy of the couplings, made by its first sweep.  New
-    couplings after that -- uploaded (fp32 or fp64) or generated on the
-    device, the copy rebuilt before the next sweep -- must read back exactly
-    and sweep bit for bit as with the global kernel."""
+    couplings after that -- uploaded (fp32 or fp64: the upload writes the
+    copy too) or generated on the device (the copy rebuilt before the next
+    sweep) -- must read back exactly and sweep bit for bit as with the
+    global kernel."""
     L = 40
     J1 = inputs.gaussian_couplings(L, seed=41, dtype=np.float32)
     J2 = inputs.gaussian_couplings(L, seed=42)
