@@ -38,15 +38,16 @@
 // periodic images of the lattice's edges, so that no box wraps; the boxes
 // land in a ring of shared-memory slots two planes ahead of their use and
 // complete on mbarriers, with bounded waits.  The bond loads then leave the
-// SM's load/store pipe and its registers, and the colour-1 planes and old
-// spins run two planes ahead as well: 148 us against 155 us per sweep at
-// L = 256, bit-identical.  Smaller lattices load each site's bonds into
-// registers a step ahead (the kernel's other instantiation).
+// SM's load/store pipe and its registers, and so do stage 0's old spins,
+// which cp.async brings into a small shared-memory ring with the colour-1
+// planes: 142 us against 155 us per sweep at L = 256, bit-identical.
+// Smaller lattices load each site's bonds and old spin into registers a
+// step ahead (the kernel's other instantiation).
 //
 // Shape (measured on GB300 at L = 256): 16 x 14 tiles make R0 exactly nine
 // warps; three CTAs per SM (51 KB of shared memory each with register
 // bonds, the rest of the SM's unified array left to L1 for their loads;
-// 71 KB with tensor-box bonds).  Bringing the colour-1 planes in by TMA
+// 74 KB with tensor-box bonds).  Bringing the colour-1 planes in by TMA
 // instead of per-thread cp.async was slower: one 3-D tensor box per plane
 // 165 us, bulk row copies 231 us, against 155 us (register bonds).
 // The heat-bath is not blocked this way: recomputing the halo's Philox draws
@@ -70,18 +71,26 @@ constexpr int W_THREADS = R0N;             // nine warps
 constexpr int W_MIN_BLOCKS = 3;            // resident CTAs per SM (at most 72 registers)
 // Pipeline shape of the two bond paths (measured at L = 256, OR sweep; all
 // bit-identical): C1_LEAD colour-1 planes in flight beyond the three stage 0
-// reads, the old colour-0 spins of stage 0 loaded into registers SL steps
-// ahead, NS0 colour-0 ring slots (two suffice: stage 1 reads planes s and
-// s + 1 and carries s - 1), and with tensor-box bonds BOX_LEAD boxes in
-// flight beyond the two in use.  Register bonds (which stage 0 also loads
-// SL = 1 step ahead): C1_LEAD 1, NS0 3 -- 155 us; C1_LEAD 2 185 us, NS0 2
-// 174 us.  Tensor-box bonds: everything two ahead and NS0 2 -- 148 us;
-// one ahead 154.5 us; 154-161 us for the mixed depths.
+// reads, NS0 colour-0 ring slots (two suffice: stage 1 reads planes s and
+// s + 1 and carries s - 1), with tensor-box bonds BOX_LEAD boxes in flight
+// beyond the two in use, and stage 0's old colour-0 spins either loaded
+// into registers SL steps ahead or (OLD_SMEM) brought by cp.async into a
+// shared-memory ring in the colour-1 planes' groups.  Register bonds (which
+// stage 0 also loads SL = 1 step ahead): C1_LEAD 1, NS0 3 -- 155 us;
+// C1_LEAD 2 185 us, NS0 2 174 us.  Tensor-box bonds with register old
+// spins: everything two ahead 148 us, one ahead 154.5 us, mixed depths
+// 154-161 us.  With old spins in shared memory (56 registers): C1_LEAD 1
+// and BOX_LEAD 2 -- 142.2 us; both one ahead 144.6 us; C1_LEAD 2 (two CTAs
+// per SM: the rings no longer fit three) 147-156 us.
+constexpr int TMA_C1_LEAD = 1;
+constexpr bool OLD_SPIN_SMEM = true;
 template <bool TMA>
 struct WaveShape {
-  static constexpr int C1_LEAD = TMA ? 2 : 1;
+  static constexpr int C1_LEAD = TMA ? TMA_C1_LEAD : 1;
   static constexpr int SL = TMA ? 2 : 1;
   static constexpr int NS0 = TMA ? 2 : 3;
+  static constexpr bool OLD_SMEM = TMA && OLD_SPIN_SMEM;
+  static constexpr int NOLD = C1_LEAD + 1;  // old-spin ring slots: planes s + 1 .. s + 1 + C1_LEAD
   static constexpr int NS1 = 3 + C1_LEAD;
 };
 constexpr int BOX_LEAD = 2;
@@ -113,9 +122,10 @@ constexpr int PAD_X = kPadX, PAD_Y = kPadY;
 struct WaveTmaSmem {
   float4 c1[WaveShape<true>::NS1][R1N];
   float4 c0[WaveShape<true>::NS0][R0N];
+  float4 o0[WaveShape<true>::OLD_SMEM ? WaveShape<true>::NOLD : 1][R0N];  // stage 0's old spins
   float tb[NTB][TB_SLOT];
   unsigned long long bar[NTB];  // one mbarrier per ring slot
-};  // 70,816 bytes
+};  // 74,272 bytes
 static_assert(offsetof(WaveTmaSmem, tb) % 128 == 0 && offsetof(WaveTmaSmem, bar) % 8 == 0, "slot alignment");
 
 template <bool TMA>
@@ -249,6 +259,8 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
   using Smem = std::conditional_t<TMA, WaveTmaSmem, WaveSmem>;
   constexpr int C1_LEAD = WaveShape<TMA>::C1_LEAD, SL = WaveShape<TMA>::SL;
   constexpr int NS0 = WaveShape<TMA>::NS0, NS1 = WaveShape<TMA>::NS1;
+  constexpr bool OLD_SMEM = WaveShape<TMA>::OLD_SMEM;
+  constexpr int NOLD = WaveShape<TMA>::NOLD;
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   float4(*c1s)[R1N] = sm.c1;
   float4(*c0s)[R0N] = sm.c0;
@@ -316,8 +328,15 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
   auto load0 = [&](uint32_t z, SiteBonds& b, float3& s) {
     const uint32_t zo = z * plane;
     if constexpr (!TMA) b = load_bonds(j0, j1, Nh2, o0, (y_0 + z) & 1u, zo, z_below(z) * plane);
-    const float4 v = ld_early4(src0 + zo + o0.off);
-    s = make_float3(v.x, v.y, v.z);
+    if constexpr (!OLD_SMEM) {
+      const float4 v = ld_early4(src0 + zo + o0.off);
+      s = make_float3(v.x, v.y, v.z);
+    }
+  };
+  // (OLD_SMEM) stage 0's old spin on plane z into old-spin slot k: one
+  // cp.async per thread, read back only by the same thread.
+  auto load_old = [&](int k, uint32_t z) {
+    if constexpr (OLD_SMEM) cp_async16(&sm.o0[k][t], src0 + z * plane + o0.off);
   };
 
   // Tensor boxes (TMA): thread 0 issues the box of plane j; every thread
@@ -369,14 +388,18 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
   load_c1(0, zs);
   load_c1(1, z_of(zs, 1));
   load_c1(2, z_of(zs, 2));
+  load_old(1 % NOLD, z_of(zs, 1));
   cp_async_commit();
 #pragma unroll
   for (int k = 1; k < C1_LEAD; ++k) {  // one group per plane beyond
     load_c1(2 + k, z_of(zs, 2 + k));
+    load_old((1 + k) % NOLD, z_of(zs, 1 + k));
     cp_async_commit();
   }
-  load0(z_of(zs, 1), cb0, cs0);
-  if constexpr (SL == 2) load0(z_of(zs, 2), nb0, ns0);
+  if constexpr (!OLD_SMEM) {
+    load0(z_of(zs, 1), cb0, cs0);
+    if constexpr (SL == 2) load0(z_of(zs, 2), nb0, ns0);
+  }
   wait_box(0);
 
   for (int s = 0; s < nsteps; ++s) {
@@ -386,14 +409,18 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     const uint32_t z1p = z_of(zs, 1), z2p = z_of(zs, 2);
     cp_async_wait<C1_LEAD - 1>();  // colour-1 planes up to s + 2
     __syncthreads();  // ... visible to all; step s-1 is done with the slots refilled next
-    if (s + 2 + C1_LEAD <= nsteps + 1) load_c1((s + 2 + C1_LEAD) % NS1, z_of(zs, 2 + C1_LEAD));
+    if (s + 2 + C1_LEAD <= nsteps + 1) {  // (and the old spins of plane s + 1 + C1_LEAD <= nsteps)
+      load_c1((s + 2 + C1_LEAD) % NS1, z_of(zs, 2 + C1_LEAD));
+      load_old((s + 1 + C1_LEAD) % NOLD, z_of(zs, 1 + C1_LEAD));
+    }
     cp_async_commit();
     // TMA: the box of plane s + 1 + BOX_LEAD into the slot of plane s - 1
     // (done with at step s - 1), and the wait for plane s + 1, stage 0's.
     if (t == 0 && box_ok && s + 1 + BOX_LEAD <= nsteps) issue_box(s + 1 + BOX_LEAD, z_of(zs, 1 + BOX_LEAD));
     wait_box(s + 1);
     // Register inputs of stage 0, SL steps ahead.
-    if constexpr (SL == 2) {
+    if constexpr (OLD_SMEM) {
+    } else if constexpr (SL == 2) {
       if (s + 2 < nsteps) load0(z_of(zs, 3), nb0, n2s0);
     } else {
       if (s + 1 < nsteps) load0(z2p, nb0, ns0);
@@ -441,7 +468,12 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
         in.jzp = cb0.zp;
         in.jzm = cb0.zm;
       }
-      in.s = cs0;
+      if constexpr (OLD_SMEM) {
+        const float4 o = sm.o0[(s + 1) % NOLD][t];
+        in.s = make_float3(o.x, o.y, o.z);
+      } else {
+        in.s = cs0;
+      }
       in.q = 0;
       in.site = 0;  // over-relaxation draws no random numbers
       const float4 v = site_result<U_OR>(in, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
@@ -540,9 +572,11 @@ constexpr int W_CARVEOUT_PCT = 58;
 // With tensor-box bonds stage 0's bond loads no longer pass through L1: the
 // carveout is the smallest that holds three CTAs (each with the 1 KB the
 // system reserves), as a percentage of the 228 KB maximum, which the driver
-// rounds up to a supported configuration (70.8 KB per CTA: 93 % -> 228 KB).
+// rounds up to a supported configuration (74.3 KB per CTA: 97 % -> 228 KB).
 constexpr int W_TMA_CARVEOUT_PCT =
-    (int)((100 * W_MIN_BLOCKS * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472);
+    (int)((100 * W_MIN_BLOCKS * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472) > 100
+        ? 100
+        : (int)((100 * W_MIN_BLOCKS * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472);
 constexpr int W_GRID_PER_SM = 3;
 
 // The kernel attributes are per device: applied once on each device used.
