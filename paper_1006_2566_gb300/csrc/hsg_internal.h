@@ -131,7 +131,7 @@ constexpr int kPadX = 2, kPadY = 2;  // halo columns / rows of the padded copy o
 __host__ __device__ inline uint32_t padded_width(int L) { return (uint32_t)((L / 2 + kPadX + 2 + 3) / 4 * 4); }
 size_t padded_bonds_elems(int L);
 cudaError_t launch_pad_bonds(const float* J, float* Jp, int L, cudaStream_t s);
-// The tensor map of Jp (4-D: xp, yp, z, a; box 24 x 17 x 1 x 6 floats).
+// The tensor map of Jp (4-D: xp, yp, z, a; box 20 x 17 x 1 x 6 floats).
 cudaError_t encode_padded_bond_map(CUtensorMap* map, const float* Jp, int L);
 
 // Spin layouts (hsg_device.cuh): `packed` = three fp32 component arrays per

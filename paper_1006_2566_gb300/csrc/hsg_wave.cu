@@ -49,7 +49,12 @@
 // bonds, the rest of the SM's unified array left to L1 for their loads;
 // 74 KB with tensor-box bonds).  Bringing the colour-1 planes in by TMA
 // instead of per-thread cp.async was slower: one 3-D tensor box per plane
-// 165 us, bulk row copies 231 us, against 155 us (register bonds).
+// 165 us, bulk row copies 231 us, against 155 us (register bonds).  With
+// tensor-box bonds, spin boxes (colour-1 planes and old spins) for the
+// tiles whose regions do not wrap -- two thirds of them at L = 256, the
+// rest on cp.async -- gave 145.8 us, and 144.3 us with that code present
+// but switched off, against 142 us without it: the wrapping tiles still set
+// the time, and the extra code cost 8 registers.
 // The heat-bath is not blocked this way: recomputing the halo's Philox draws
 // and transcendentals made it compute-bound and slower than two half-sweeps.
 #include <cstddef>
