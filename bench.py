@@ -91,7 +91,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "serving"], default="l256_hb_or")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batched", "l16_pooled", "serving"],
+                    default="l256_hb_or")
     ap.add_argument("--kernel", choices=["auto", "global", "slab", "wave"], default="auto")
     ap.add_argument("--layout", choices=["float4", "packed"], default="float4", help="device spin layout")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the timed oracle sample")
@@ -99,7 +100,7 @@ def parse_args():
     ap.add_argument("--no-clocks", action="store_true", help="do not sample nvidia-smi")
     ap.add_argument("--no-autotune", action="store_true", help="batched workload: default pool launch shape")
     ap.add_argument("--no-batched", action="store_true",
-                    help="default line: skip the batched-pool summary (512 samples x 2 replicas)")
+                    help="default line: skip the batched-pool summaries (512 samples x 2 replicas; 2048 L=16 samples)")
     ap.add_argument("--no-serving", action="store_true", help="default line: skip the serving summary")
     return ap.parse_args()
 
@@ -554,6 +555,10 @@ def run_ours(args, wl):
                                                 "hit_updates_per_ns", "lattices", "sites", "autotuned",
                                                 "gpu_launches")}
             out["batched"]["workload"] = BATCH["desc"]
+            p = measure_batched(steps=20, warmup=3, cfg=BATCH_L16)
+            out["l16_pooled"] = {k: p[k] for k in ("value", "unit", "speedup_vs_plain", "plain_one_lattice_per_launch",
+                                                   "lattices", "sites", "autotuned", "gpu_launches")}
+            out["l16_pooled"]["workload"] = BATCH_L16["desc"]
         if not args.no_serving:
             m = measure_serving()
             o, sub, fifo, same = (m["overload"], m["sub_saturating"], m["plain_fifo_one_per_launch"],
@@ -790,38 +795,49 @@ def run_reference(args, wl):
 # Batched workload: many small lattices in one pool
 # ---------------------------------------------------------------------------
 
-BATCH = dict(samples=512, replicas=2, sides=(16, 24, 32, 48), seed=4, hits=4, step=0.5, n_or=2, renorm_every=10,
-             sweeps_per_step=10,
+BATCH = dict(samples=512, replicas=2, sides=(16, 24, 32, 48), seed=4, hits=4, proposal="BALL", step=0.5, n_or=2,
+             renorm_every=10, sweeps_per_step=10, T=None,
              desc=("batched: 512 samples x 2 replicas, L uniform in {16,24,32,48} (seeded), T_s = 0.2 + 0.8 s/511, "
                    "Gaussian J per sample (device Philox + Box-Muller), 4-hit Metropolis (ball, 0.5) + 2 OR per "
                    "sweep, renorm every 10; one pool, one graph replay per sweep; 1 step = 10 sweeps"))
+# The L = 16 single-lattice workload (l16_met: 1-hit Metropolis, uniform-
+# sphere proposal, T = 1) as it is meant to run: many independent samples
+# in one pool.
+BATCH_L16 = dict(samples=2048, replicas=1, sides=(16,), seed=1, hits=1, proposal="SPHERE", step=0.5, n_or=0,
+                 renorm_every=0, sweeps_per_step=10, T=1.0,
+                 desc=("pooled L=16: 2048 independent samples of the L=16 workload (Gaussian J per sample from device "
+                       "Philox + Box-Muller; checkerboard Metropolis 1 hit, uniform-sphere proposal, T=1.0), one pool, "
+                       "one graph replay per sweep; 1 step = 10 sweeps"))
 
 
-def batch_specs():
-    """(L, seed, sample, replica, T) of every lattice of the batched workload."""
-    rng = np.random.default_rng([BATCH["seed"], 0x4C])
-    sides = rng.choice(BATCH["sides"], size=BATCH["samples"])
+def batch_specs(cfg=BATCH):
+    """(L, seed, sample, replica, T) of every lattice of a batched workload:
+    sides drawn from cfg["sides"] (seeded), T fixed or ramped over the
+    samples from 0.2 to 1.0."""
+    rng = np.random.default_rng([cfg["seed"], 0x4C])
+    sides = rng.choice(cfg["sides"], size=cfg["samples"])
     out = []
-    for s in range(BATCH["samples"]):
-        T = 0.2 + 0.8 * s / (BATCH["samples"] - 1)
-        for r in range(BATCH["replicas"]):
-            out.append((int(sides[s]), BATCH["seed"], s, r, T))
+    for s in range(cfg["samples"]):
+        T = cfg["T"] if cfg["T"] is not None else 0.2 + 0.8 * s / (cfg["samples"] - 1)
+        for r in range(cfg["replicas"]):
+            out.append((int(sides[s]), cfg["seed"], s, r, T))
     return out
 
 
-def measure_batched(steps: int, warmup: int, autotune: bool = True) -> dict:
-    """The batched workload in one pool (graph-replayed sweeps, autotuned
+def measure_batched(steps: int, warmup: int, autotune: bool = True, cfg=BATCH) -> dict:
+    """A batched workload in one pool (graph-replayed sweeps, autotuned
     launch shape) against one lattice per launch, on the current device."""
     import torch
 
     from paper_1006_2566_gb300 import hsg
 
-    specs = batch_specs()
+    specs = batch_specs(cfg)
     sites = sum(L ** 3 for L, *_ in specs)
-    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=BATCH["hits"], proposal=hsg.HSG_PROP_BALL, step=BATCH["step"],
-                         n_or=BATCH["n_or"], renorm_every=BATCH["renorm_every"])
-    sps = BATCH["sweeps_per_step"]
-    passes = 1 + BATCH["n_or"]
+    prop = hsg.HSG_PROP_BALL if cfg["proposal"] == "BALL" else hsg.HSG_PROP_SPHERE
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=cfg["hits"], proposal=prop, step=cfg["step"],
+                         n_or=cfg["n_or"], renorm_every=cfg["renorm_every"])
+    sps = cfg["sweeps_per_step"]
+    passes = 1 + cfg["n_or"]
     stream = torch.cuda.Stream()
     budget = int(sum(28 * L ** 3 for L, *_ in specs) * 1.05) + (1 << 24)
     with hsg.Pool(budget, len(specs), stream) as pool:
@@ -829,10 +845,10 @@ def measure_batched(steps: int, warmup: int, autotune: bool = True) -> dict:
             pool.admit(*spec)
         t0 = time.perf_counter()
         if not autotune:
-            cfg = (256, 512, 8, 0)  # the pool's default launch configuration
-            hsg.hsg_pool_config(pool.pool, *cfg)
+            tcfg = (256, 512, 8, 0)  # the pool's default launch configuration
+            hsg.hsg_pool_config(pool.pool, *tcfg)
         else:
-            cfg = hsg.hsg_pool_autotune(pool.pool, sched)
+            tcfg = hsg.hsg_pool_autotune(pool.pool, sched)
         tune_s = time.perf_counter() - t0
         for _ in range(warmup):
             pool.sweep(sched, sps)
@@ -856,9 +872,8 @@ def measure_batched(steps: int, warmup: int, autotune: bool = True) -> dict:
     for (L, seed, sample, replica, T) in sub:
         lat = hsg.Lattice(L, seed, sample, replica, stream)
         lat.generate_couplings()
-        ctxs.append((lat, hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=BATCH["hits"], proposal=hsg.HSG_PROP_BALL,
-                                       step=BATCH["step"], n_or=BATCH["n_or"], T=T,
-                                       renorm_every=BATCH["renorm_every"])))
+        ctxs.append((lat, hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=cfg["hits"], proposal=prop, step=cfg["step"],
+                                       n_or=cfg["n_or"], T=T, renorm_every=cfg["renorm_every"])))
     for lat, s in ctxs:
         lat.sweep(s, 1)
     torch.cuda.synchronize()
@@ -873,9 +888,9 @@ def measure_batched(steps: int, warmup: int, autotune: bool = True) -> dict:
     plain = sub_sites * passes * sps / (plain_ms * 1e6)
     return {"value": round(value, 4), "unit": "spin updates/ns", "steps": steps, "ms_per_step": round(ms / steps, 4),
             "lattices": len(specs), "sites": sites,
-            "autotuned": {"threads": cfg[0], "tile_sites": cfg[1], "blocks_per_sm": cfg[2],
-                          "hits_per_pass": cfg[3] or BATCH["hits"], "seconds": round(tune_s, 3)} if autotune else None,
-            "hit_updates_per_ns": round(sites * (BATCH["hits"] + BATCH["n_or"]) * sps * steps / (ms * 1e6), 4),
+            "autotuned": {"threads": tcfg[0], "tile_sites": tcfg[1], "blocks_per_sm": tcfg[2],
+                          "hits_per_pass": tcfg[3] or cfg["hits"], "seconds": round(tune_s, 3)} if autotune else None,
+            "hit_updates_per_ns": round(sites * (cfg["hits"] + cfg["n_or"]) * sps * steps / (ms * 1e6), 4),
             "plain_one_lattice_per_launch": {"value": round(plain, 4), "unit": "spin updates/ns",
                                              "lattices": len(sub), "sites": sub_sites,
                                              "ms_for_10_sweeps": round(plain_ms, 3)},
@@ -883,20 +898,20 @@ def measure_batched(steps: int, warmup: int, autotune: bool = True) -> dict:
             "energy_per_spin_mean": float(np.nanmean(energies))}
 
 
-def run_batched(args):
+def run_batched(args, cfg=BATCH):
     import torch
 
     from paper_1006_2566_gb300 import build
 
     build.build()
     torch.cuda.set_device(0)
-    b = measure_batched(args.steps, args.warmup, not args.no_autotune)
+    b = measure_batched(args.steps, args.warmup, not args.no_autotune, cfg)
     out = {
         "metric": "spin updates/ns", "value": b["value"], "unit": "spin updates/ns", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": b["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: seeded sides and temperatures, couplings and spins from Philox",
-        "config": {"workload": BATCH["desc"], "lattices": b["lattices"], "sites": b["sites"],
+        "config": {"workload": cfg["desc"], "lattices": b["lattices"], "sites": b["sites"],
                    "autotuned": b["autotuned"]},
         "hit_updates_per_ns": b["hit_updates_per_ns"],
         "plain_one_lattice_per_launch": b["plain_one_lattice_per_launch"],
@@ -977,8 +992,8 @@ def run_serving(args):
 
 def main():
     args = parse_args()
-    if args.workload == "batched":
-        run_batched(args)
+    if args.workload in ("batched", "l16_pooled"):
+        run_batched(args, BATCH if args.workload == "batched" else BATCH_L16)
         return
     if args.workload == "serving":
         run_serving(args)

@@ -341,3 +341,28 @@ def test_pool_sweeps_match_oracle_layer_by_layer(hsg):
             L = spec[0]
             ref = oracle.energy(L, Js[spec], pool.spins(slot).astype(np.float64)) / L ** 3
             assert abs(e[slot] - ref) <= 2e-6, spec
+
+
+def test_pooled_l16_metropolis_matches_oracle_layer_by_layer(hsg):
+    """The L = 16 single-lattice workload (1-hit Metropolis, uniform-sphere
+    proposal, T = 1) run as the benchmark pools it: independent samples in
+    one pool under the autotuned launch shape.  Two sweeps of every lattice
+    are checked on every site, layer by layer, against the oracle's
+    half-sweeps from the lattice's state before the layer."""
+    from parity_rules import check_one_sweep
+
+    kw = dict(kind=hsg.HSG_METROPOLIS, hits=1, proposal=hsg.HSG_PROP_SPHERE, step=0.5)
+    specs = [(16, 1, s, 0, 1.0, s % 2 == 0) for s in range(8)]
+    Js = {spec: oracle_couplings(spec[0], spec[1], spec[2], spec[5]) for spec in specs}
+    with hsg.Pool(1 << 26, len(specs), torch.cuda.Stream()) as pool:
+        slots = {spec: pool.admit(*spec[:5], J=Js[spec] if spec[5] else None) for spec in specs}
+        hsg.hsg_pool_autotune(pool.pool, hsg.schedule(**kw))
+        for n in range(2):
+            before = {slot: pool.spins(slot) for slot in slots.values()}
+            pool.sweep(hsg.schedule(**kw), 1)
+            for spec, slot in slots.items():
+                L, seed, sample, replica, T, _ = spec
+                p = oracle.Params(key=oracle.key(seed, sample, replica), sweep=n, beta=1.0 / T, step=0.5, hits=1,
+                                  proposal=hsg.HSG_PROP_SPHERE)
+                check_one_sweep(L, Js[spec], before[slot], pool.spins(slot), oracle.MET, p,
+                                label=f"pooled L=16 sample {sample} sweep {n}")
