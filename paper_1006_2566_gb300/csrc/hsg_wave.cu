@@ -10,19 +10,18 @@
 //   stage 0: reflects colour 0 on plane k+1 over the tile grown by one site
 //            on every side (region R0, one thread per site), from the old
 //            colour-1 planes k, k+1, k+2 (region R1, the tile grown by two
-//            sites: a ring of four plane tiles in shared memory, filled by
-//            cp.async one plane ahead);
+//            sites: a ring of plane tiles in shared memory, filled by
+//            cp.async ahead of their use);
 //   stage 1: reflects colour 1 on plane k over the tile, from the new colour-0
-//            planes k-1, k, k+1 (a ring of three in shared memory).
-// The bonds and old spins of stage 0 are loaded into registers one step
-// ahead; stage 0 leaves its bonds in shared memory, where stage 1 finds its
-// own (each bond joins a colour-0 and a colour-1 site).  Each spin and bond
-// thus leaves HBM about once per full sweep instead of once per half-sweep:
-// 44 B per site update instead of 72 B.  A thread marches up one column, so
-// the neighbours in its own column on three consecutive planes (its -z, one
-// x and its +z neighbour) are read from shared memory once and carried in
-// registers: four shared-memory reads per site instead of six.  The RENORM
-// instantiation also renormalises every spin it stores, for a
+//            planes k-1, k, k+1 (a ring in shared memory).
+// Each bond joins a colour-0 and a colour-1 site, so both stages read their
+// bonds from one shared-memory copy of the plane's bonds.  Each spin and
+// bond thus leaves HBM about once per full sweep instead of once per
+// half-sweep: 44 B per site update instead of 72 B.  A thread marches up one
+// column, so the neighbours in its own column on three consecutive planes
+// (its -z, one x and its +z neighbour) are read from shared memory once and
+// carried in registers: four shared-memory reads per site instead of six.
+// The RENORM instantiations also renormalise every spin they store, for a
 // renormalisation due right after the sweep.
 //
 // Neighbouring tiles both compute the colour-0 sites of their shared halo;
@@ -32,34 +31,34 @@
 // buffer to another.  The result equals colour 0 then colour 1 of
 // launch_half_sweep exactly.
 //
-// Bonds: from L = 32 (and when the device has room for it) each plane's
-// bonds come as ONE tensor box per CTA (TMA, cp.async.bulk.tensor) from a
-// halo-padded copy of the couplings whose rows and columns carry the
-// periodic images of the lattice's edges, so that no box wraps; the boxes
-// land in a ring of shared-memory slots two planes ahead of their use and
-// complete on mbarriers, with bounded waits.  The bond loads then leave the
-// SM's load/store pipe and its registers, and so do stage 0's old spins,
-// which cp.async brings into a small shared-memory ring with the colour-1
-// planes: 142 us against 155 us per sweep at L = 256, bit-identical.
-// Smaller lattices load each site's bonds and old spin into registers a
-// step ahead (the kernel's other instantiation).
+// Two kernels, bit-identical to each other:
+//   k_or_sweep_wave (from L = 32, when the device has room for a halo-padded
+//     copy of the couplings): each plane's bonds come as ONE tensor box per
+//     CTA (TMA, cp.async.bulk.tensor) from the padded copy, whose rows and
+//     columns carry the periodic images of the lattice's edges so that no
+//     box wraps; the colour-1 planes come by cp.async completing on
+//     mbarriers; stage 0's old spins by cp.async into the slot where its new
+//     value goes.  One CTA barrier per plane (the pipeline is described at
+//     the kernel).  135.6 us per sweep at L = 256.
+//   k_or_sweep_wave_regs (smaller lattices, or no room for the copy): stage
+//     0 loads each site's bonds and old spin into registers a step ahead and
+//     leaves the bonds in shared memory for stage 1; two barriers per plane.
+//     155 us at L = 256.
 //
 // Shape (measured on GB300 at L = 256): 16 x 14 tiles make R0 exactly nine
-// warps; three CTAs per SM (51 KB of shared memory each with register
-// bonds, the rest of the SM's unified array left to L1 for their loads;
-// 74 KB with tensor-box bonds).  Bringing the colour-1 planes in by TMA
-// instead of per-thread cp.async was slower: one 3-D tensor box per plane
-// 165 us, bulk row copies 231 us, against 155 us (register bonds).  With
-// tensor-box bonds, spin boxes (colour-1 planes and old spins) for the
-// tiles whose regions do not wrap -- two thirds of them at L = 256, the
-// rest on cp.async -- gave 145.8 us, and 144.3 us with that code present
-// but switched off, against 142 us without it: the wrapping tiles still set
-// the time, and the extra code cost 8 registers.
+// warps; three CTAs per SM (74 KB of shared memory each for the tensor-box
+// kernel; 51 KB for the register kernel, the rest of the SM's unified array
+// left to L1 for its loads).  Measured and dropped (bit-identical, slower):
+// the colour-1 planes by one 3-D tensor box per plane (165 us against 155
+// us, register bonds) or by bulk row copies (231 us); with tensor-box bonds
+// and two barriers per plane (142 us), spin boxes for the tiles whose
+// regions do not wrap (145.8 us; the wrapping tiles, still on cp.async,
+// set the time), tiles of 32 x 14 or 16 x 30 at two CTAs per SM (149, 159
+// us), deeper or shallower rings (144.6-185 us).
 // The heat-bath is not blocked this way: recomputing the halo's Philox draws
 // and transcendentals made it compute-bound and slower than two half-sweeps.
 #include <cstddef>
 #include <mutex>
-#include <type_traits>
 
 #include "hsg_device.cuh"
 #include "hsg_internal.h"
@@ -74,69 +73,41 @@ constexpr int R0X = WX + 2, R0Y = WY + 2;  // colour-0 region: halo 1
 constexpr int R0N = R0X * R0Y;             // 288
 constexpr int W_THREADS = R0N;             // nine warps
 constexpr int W_MIN_BLOCKS = 3;            // resident CTAs per SM (at most 72 registers)
-// Pipeline shape of the two bond paths (measured at L = 256, OR sweep; all
-// bit-identical): C1_LEAD colour-1 planes in flight beyond the three stage 0
-// reads, NS0 colour-0 ring slots (two suffice: stage 1 reads planes s and
-// s + 1 and carries s - 1), with tensor-box bonds BOX_LEAD boxes in flight
-// beyond the two in use, and stage 0's old colour-0 spins either loaded
-// into registers SL steps ahead or (OLD_SMEM) brought by cp.async into a
-// shared-memory ring in the colour-1 planes' groups.  Register bonds (which
-// stage 0 also loads SL = 1 step ahead): C1_LEAD 1, NS0 3 -- 155 us;
-// C1_LEAD 2 185 us, NS0 2 174 us.  Tensor-box bonds with register old
-// spins: everything two ahead 148 us, one ahead 154.5 us, mixed depths
-// 154-161 us.  With old spins in shared memory (56 registers): C1_LEAD 1
-// and BOX_LEAD 2 -- 142.2 us; both one ahead 144.6 us; C1_LEAD 2 (two CTAs
-// per SM: the rings no longer fit three) 147-156 us.
-constexpr int TMA_C1_LEAD = 1;
-constexpr bool OLD_SPIN_SMEM = true;
-template <bool TMA>
-struct WaveShape {
-  static constexpr int C1_LEAD = TMA ? TMA_C1_LEAD : 1;
-  static constexpr int SL = TMA ? 2 : 1;
-  static constexpr int NS0 = TMA ? 2 : 3;
-  static constexpr bool OLD_SMEM = TMA && OLD_SPIN_SMEM;
-  static constexpr int NOLD = C1_LEAD + 1;  // old-spin ring slots: planes s + 1 .. s + 1 + C1_LEAD
-  static constexpr int NS1 = 3 + C1_LEAD;
-};
-constexpr int BOX_LEAD = 2;
 constexpr int MIN_ZC = 8;                  // shortest z chunk
 static_assert(W_THREADS % 32 == 0 && WX * WY <= W_THREADS && R1N <= 2 * W_THREADS, "thread roles");
 
-// Bond slots of an R0 site: its +x, +y, +z bonds and its -x, -y, -z bonds.
+// Register kernel.  Bond slots of an R0 site: its +x, +y, +z bonds and its
+// -x, -y, -z bonds.
 enum { B_XP = 0, B_YP = 1, B_ZP = 2, B_XM = 3, B_YM = 4, B_ZM = 5, NB = 6 };
-
+constexpr int NS1_REGS = 4, NS0_REGS = 3;  // colour-1 ring (one plane in flight), colour-0 ring
 struct WaveSmem {
-  float4 c1[WaveShape<false>::NS1][R1N];  // old colour 1 over R1
-  float4 c0[WaveShape<false>::NS0][R0N];  // new colour 0 over R0
-  float jb[2][NB][R0N];  // bonds of the R0 sites of two planes
+  float4 c1[NS1_REGS][R1N];  // old colour 1 over R1
+  float4 c0[NS0_REGS][R0N];  // new colour 0 over R0
+  float jb[2][NB][R0N];      // bonds of the R0 sites of two planes
 };  // 51,264 bytes
 
-// Tensor-box bonds: one box per plane holds all six bond arrays
-// (a = 2d + c) of the rows y0 - 2 .. y0 + 14 and the columns xh0 - 2 ..
-// xh0 + 17 of the halo-padded copy -- every bond any site of the CTA's
-// two stages needs on that plane.  Box element (a, row k, col m) is the bond
-// of (y0 - 2 + k, xh0 - 2 + m).  A ring of three planes (s, s + 1 in use,
-// s + 2 .. s + 1 + BOX_LEAD in flight), each slot rounded up to 128 bytes.
+// Tensor-box kernel.  One box per plane holds all six bond arrays (a = 2d +
+// c) of the rows y0 - 2 .. y0 + 14 and the columns xh0 - 2 .. xh0 + 17 of
+// the halo-padded copy -- every bond any site of the CTA's two stages needs
+// on that plane.  Box element (a, row k, col m) is the bond of (y0 - 2 + k,
+// xh0 - 2 + m).  Each slot is rounded up to 128 bytes.
 constexpr int TB_X = WX + 4, TB_Y = WY + 3, TB_A = 6;  // 20 x 17 x 6 floats
 static_assert(TB_X % 4 == 0, "a box row is a multiple of 16 bytes");
 constexpr int TB_ARRAY = TB_X * TB_Y;                      // 340 floats
 constexpr uint32_t TB_BYTES = TB_A * TB_ARRAY * 4;         // 8160
 constexpr int TB_SLOT = (TB_BYTES + 127) / 128 * 128 / 4;  // 2048 floats
-constexpr int NTB = 2 + BOX_LEAD;
 constexpr int PAD_X = kPadX, PAD_Y = kPadY;
-struct WaveTmaSmem {
-  float4 c1[WaveShape<true>::NS1][R1N];
-  float4 c0[WaveShape<true>::NS0][R0N];
-  float4 o0[WaveShape<true>::OLD_SMEM ? WaveShape<true>::NOLD : 1][R0N];  // stage 0's old spins
-  float tb[NTB][TB_SLOT];
-  unsigned long long bar[NTB];  // one mbarrier per ring slot
-};  // 74,272 bytes
-static_assert(offsetof(WaveTmaSmem, tb) % 128 == 0 && offsetof(WaveTmaSmem, bar) % 8 == 0, "slot alignment");
-
-template <bool TMA>
-constexpr size_t wave_smem() {
-  return TMA ? sizeof(WaveTmaSmem) : sizeof(WaveSmem);
-}
+constexpr int NR = 4;  // ring depth of every buffer of the tensor-box kernel
+struct WaveBoxSmem {
+  float4 c1[NR][R1N];  // old colour 1, plane j in slot j % NR
+  float4 c0[NR][R0N];  // colour 0 of plane j: its old spins, then its new ones
+  float tb[NR][TB_SLOT];
+  unsigned long long bar[NR];   // bond boxes
+  unsigned long long full[NR];  // colour-1 planes
+};  // 74,304 bytes
+static_assert(offsetof(WaveBoxSmem, c0) % 128 == 0 && offsetof(WaveBoxSmem, tb) % 128 == 0 &&
+                  offsetof(WaveBoxSmem, bar) % 8 == 0,
+              "slot alignment");
 
 inline unsigned cdiv(long long a, long long b) { return (unsigned)((a + b - 1) / b); }
 
@@ -247,26 +218,20 @@ __device__ __forceinline__ SiteBonds load_bonds(const float* __restrict__ jc, co
   return b;
 }
 
-// RENORM: the stored spins are renormalised (renorm_spin), as by a
-// renormalisation pass right after the sweep; the colour-0 values that
-// stage 1 reads from shared memory are the unrenormalised ones, as in the
-// unfused order.
-// TMA: each plane's bonds come as one tensor box of the halo-padded copy
-// (bond_map) into a ring of three shared-memory slots, issued by thread 0
-// two planes ahead and completing on one mbarrier per slot; stage 0 and
-// stage 1 read their bonds there.  Otherwise stage 0 loads its bonds into
-// registers a step ahead and leaves them in shared memory for stage 1.
-// Both read the same bond values, so the results are the same bit for bit.
-template <bool RENORM, bool TMA>
-__global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
-    k_or_sweep_wave(const WaveArgs a, int zc, const __grid_constant__ CUtensorMap bond_map) {
+// Arrive on `bar` once this thread's cp.async copies issued so far have
+// landed (the barrier's count includes the arrival).
+__device__ __forceinline__ void cp_async_arrive(unsigned long long* bar) {
+  asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// The register kernel: stage 0 loads its bonds and old spin into registers
+// a step ahead and leaves the bonds in shared memory for stage 1; the
+// colour-1 planes come by cp.async one plane ahead.
+template <bool RENORM>
+__global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave_regs(const WaveArgs a, int zc) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  using Smem = std::conditional_t<TMA, WaveTmaSmem, WaveSmem>;
-  constexpr int C1_LEAD = WaveShape<TMA>::C1_LEAD, SL = WaveShape<TMA>::SL;
-  constexpr int NS0 = WaveShape<TMA>::NS0, NS1 = WaveShape<TMA>::NS1;
-  constexpr bool OLD_SMEM = WaveShape<TMA>::OLD_SMEM;
-  constexpr int NOLD = WaveShape<TMA>::NOLD;
-  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+  WaveSmem& sm = *reinterpret_cast<WaveSmem*>(smem_raw);
+  constexpr int NS0 = NS0_REGS, NS1 = NS1_REGS;
   float4(*c1s)[R1N] = sm.c1;
   float4(*c0s)[R0N] = sm.c0;
 
@@ -312,13 +277,9 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
   const uint32_t off1 = y_1 * Lhu + xh_1;
   const int b0 = (r1 + 1) * R0X + (cc1 + 1);    // in R0 coordinates (valid1 only)
   const int own1 = (r1 + 2) * R1X + (cc1 + 2);  // in R1 coordinates (valid1 only)
-  // Box positions of the two sites (TMA): row y - (y0 - 2), column xh - (xh0 - 2).
-  const int tb0 = (r0 + 1) * TB_X + (cc0 + 1);
-  const int tb1 = (r1 + 2) * TB_X + (cc1 + 2);
 
   // Planes are numbered j = 0, 1, ... from z0 - 2; the colour-1 tile of
-  // plane j sits in c1 slot j % NS1, the new colour-0 tile in c0 slot j % NS0
-  // and (TMA) its bond box in tb slot j % NTB.
+  // plane j sits in c1 slot j % NS1, the new colour-0 tile in c0 slot j % NS0.
   // z_of(zs, k): the plane k after plane zs, wrapped (k <= 3 < L).
   auto z_of = [&](uint32_t zs, uint32_t k) { return zs + k >= Lu ? zs + k - Lu : zs + k; };
   auto z_below = [&](uint32_t z) { return z == 0 ? Lu - 1 : z - 1; };
@@ -328,108 +289,37 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     cp_async16(&slot[t], src1 + zo + l1_off[0]);
     if (l1_second) cp_async16(&slot[t + W_THREADS], src1 + zo + l1_off[1]);
   };
-  // Register inputs of stage 0 on plane z: its bonds (unless they come by
-  // tensor box) and old spin.
+  // Register inputs of stage 0 on plane z: its bonds and old spin.
   auto load0 = [&](uint32_t z, SiteBonds& b, float3& s) {
     const uint32_t zo = z * plane;
-    if constexpr (!TMA) b = load_bonds(j0, j1, Nh2, o0, (y_0 + z) & 1u, zo, z_below(z) * plane);
-    if constexpr (!OLD_SMEM) {
-      const float4 v = ld_early4(src0 + zo + o0.off);
-      s = make_float3(v.x, v.y, v.z);
-    }
-  };
-  // (OLD_SMEM) stage 0's old spin on plane z into old-spin slot k: one
-  // cp.async per thread, read back only by the same thread.
-  auto load_old = [&](int k, uint32_t z) {
-    if constexpr (OLD_SMEM) cp_async16(&sm.o0[k][t], src0 + z * plane + o0.off);
-  };
-
-  // Tensor boxes (TMA): thread 0 issues the box of plane j; every thread
-  // waits for it before reading it.  A wait that gives up marks the
-  // sweep as failed (a.err), stops further boxes and waits, and lets the
-  // CTA run to its end; thread 0 then waits, again bounded, for the boxes
-  // still in flight, so that none lands after the CTA has exited.
-  bool box_ok = true;
-  int boxes_issued = 0, boxes_seen = 0;
-  auto issue_box = [&](int j, uint32_t z) {
-    if constexpr (TMA) {
-      const int k = j % NTB;
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of the slot, then the box
-      mbar_expect_tx(&sm.bar[k], TB_BYTES + a.box_extra_tx);
-      tma_box_4d(sm.tb[k], &bond_map, xh0, y0, (int)z, 0, &sm.bar[k]);
-      boxes_issued = j + 1;
-    }
-  };
-  auto wait_box = [&](int j) {
-    if constexpr (TMA) {
-      if (!box_ok) return;
-      if (mbar_wait_bounded(&sm.bar[j % NTB], (uint32_t)(j / NTB) & 1u, kBoxWaitNs)) {
-        boxes_seen = j + 1;
-      } else {
-        box_ok = false;
-        atomicOr(a.err, 1ull);
-      }
-    }
+    b = load_bonds(j0, j1, Nh2, o0, (y_0 + z) & 1u, zo, z_below(z) * plane);
+    const float4 v = ld_early4(src0 + zo + o0.off);
+    s = make_float3(v.x, v.y, v.z);
   };
 
   SiteBonds cb0{}, nb0{};
   float jzm1 = 0.0f;  // stage 1: the -z bond of this column, from the plane before
-  float3 cs0 = make_float3(0.0f, 0.0f, 0.0f), ns0 = cs0, n2s0 = cs0;  // stage 0's old spins, planes s + 1 ..
+  float3 cs0 = make_float3(0.0f, 0.0f, 0.0f), ns0 = cs0;  // stage 0's old spins, planes s + 1, s + 2
   // Column carries: stage 0's old colour 1 on planes s, s + 1 (a0, a1),
   // stage 1's new colour 0 on planes s - 1, s (bm, bc).
   float4 a0 = make_float4(0.0f, 0.0f, 0.0f, 0.0f), a1 = a0, bm = a0, bc = a0;
   uint32_t zs = (uint32_t)wrap_mod(z0 - 2, L);  // plane of j = s
-  if constexpr (TMA) {
-    if (t == 0) {
-#pragma unroll
-      for (int k = 0; k < NTB; ++k) mbar_init(&sm.bar[k], 1);
-      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    }
-    __syncthreads();
-    if (t == 0)
-#pragma unroll
-      for (int j = 0; j <= BOX_LEAD; ++j) issue_box(j, z_of(zs, j));
-  }
   load_c1(0, zs);
   load_c1(1, z_of(zs, 1));
   load_c1(2, z_of(zs, 2));
-  load_old(1 % NOLD, z_of(zs, 1));
   cp_async_commit();
-#pragma unroll
-  for (int k = 1; k < C1_LEAD; ++k) {  // one group per plane beyond
-    load_c1(2 + k, z_of(zs, 2 + k));
-    load_old((1 + k) % NOLD, z_of(zs, 1 + k));
-    cp_async_commit();
-  }
-  if constexpr (!OLD_SMEM) {
-    load0(z_of(zs, 1), cb0, cs0);
-    if constexpr (SL == 2) load0(z_of(zs, 2), nb0, ns0);
-  }
-  wait_box(0);
+  load0(z_of(zs, 1), cb0, cs0);
 
   for (int s = 0; s < nsteps; ++s) {
     // Ring slots of planes s .. s + 2 (colour 1) and s, s + 1 (colour 0).
     const int k0 = s % NS1, k1 = (s + 1) % NS1, k2 = (s + 2) % NS1;
     const int c00 = s % NS0, c0p = (s + 1) % NS0;
     const uint32_t z1p = z_of(zs, 1), z2p = z_of(zs, 2);
-    cp_async_wait<C1_LEAD - 1>();  // colour-1 planes up to s + 2
-    __syncthreads();  // ... visible to all; step s-1 is done with the slots refilled next
-    if (s + 2 + C1_LEAD <= nsteps + 1) {  // (and the old spins of plane s + 1 + C1_LEAD <= nsteps)
-      load_c1((s + 2 + C1_LEAD) % NS1, z_of(zs, 2 + C1_LEAD));
-      load_old((s + 1 + C1_LEAD) % NOLD, z_of(zs, 1 + C1_LEAD));
-    }
+    cp_async_wait<0>();  // colour-1 planes up to s + 2
+    __syncthreads();     // ... visible to all; step s-1 is done with the slot refilled next
+    if (s + 3 <= nsteps + 1) load_c1((s + 3) % NS1, z_of(zs, 3));
     cp_async_commit();
-    // TMA: the box of plane s + 1 + BOX_LEAD into the slot of plane s - 1
-    // (done with at step s - 1), and the wait for plane s + 1, stage 0's.
-    if (t == 0 && box_ok && s + 1 + BOX_LEAD <= nsteps) issue_box(s + 1 + BOX_LEAD, z_of(zs, 1 + BOX_LEAD));
-    wait_box(s + 1);
-    // Register inputs of stage 0, SL steps ahead.
-    if constexpr (OLD_SMEM) {
-    } else if constexpr (SL == 2) {
-      if (s + 2 < nsteps) load0(z_of(zs, 3), nb0, n2s0);
-    } else {
-      if (s + 1 < nsteps) load0(z2p, nb0, ns0);
-    }
+    if (s + 1 < nsteps) load0(z2p, nb0, ns0);  // stage 0's inputs, a step ahead
 
     // Stage 0: colour 0 on plane j = s + 1 (stored when s in [1, z1 - z0]).
     // Its -z, +z and one of its x neighbours sit in its own column on
@@ -454,45 +344,25 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
       in.szm = a0;
       a0 = a1;
       a1 = a2;
-      if constexpr (TMA) {
-        // Its +d bonds and the -x / -y bonds (the +x / +y bonds of its -x /
-        // -y neighbours, colour 1) on plane s + 1; the -z bond (the +z bond
-        // of the colour-1 site below) on plane s.
-        const float* B = sm.tb[(s + 1) % NTB];
-        in.jxp = B[0 * TB_ARRAY + tb0];
-        in.jxm = B[1 * TB_ARRAY + tb0 - (p ? 0 : 1)];
-        in.jyp = B[2 * TB_ARRAY + tb0];
-        in.jym = B[3 * TB_ARRAY + tb0 - TB_X];
-        in.jzp = B[4 * TB_ARRAY + tb0];
-        in.jzm = sm.tb[s % NTB][5 * TB_ARRAY + tb0];
-      } else {
-        in.jxp = cb0.xp;
-        in.jxm = cb0.xm;
-        in.jyp = cb0.yp;
-        in.jym = cb0.ym;
-        in.jzp = cb0.zp;
-        in.jzm = cb0.zm;
-      }
-      if constexpr (OLD_SMEM) {
-        const float4 o = sm.o0[(s + 1) % NOLD][t];
-        in.s = make_float3(o.x, o.y, o.z);
-      } else {
-        in.s = cs0;
-      }
+      in.jxp = cb0.xp;
+      in.jxm = cb0.xm;
+      in.jyp = cb0.yp;
+      in.jym = cb0.ym;
+      in.jzp = cb0.zp;
+      in.jzm = cb0.zm;
+      in.s = cs0;
       in.q = 0;
       in.site = 0;  // over-relaxation draws no random numbers
       const float4 v = site_result<U_OR>(in, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
       c0s[c0p][t] = v;
       if (owned0 && s >= 1 && s <= z1 - z0) dst0[z * plane + o0.off] = RENORM ? renorm_spin(v) : v;
-      if constexpr (!TMA) {
-        float(*jb)[R0N] = sm.jb[(s + 1) & 1];
-        jb[B_XP][t] = cb0.xp;
-        jb[B_YP][t] = cb0.yp;
-        jb[B_ZP][t] = cb0.zp;
-        jb[B_XM][t] = cb0.xm;
-        jb[B_YM][t] = cb0.ym;
-        jb[B_ZM][t] = cb0.zm;
-      }
+      float(*jb)[R0N] = sm.jb[(s + 1) & 1];
+      jb[B_XP][t] = cb0.xp;
+      jb[B_YP][t] = cb0.yp;
+      jb[B_ZP][t] = cb0.zp;
+      jb[B_XM][t] = cb0.xm;
+      jb[B_YM][t] = cb0.ym;
+      jb[B_ZM][t] = cb0.zm;
     }
     __syncthreads();
 
@@ -516,23 +386,12 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
       in.sym = n0[-R0X];
       in.szp = b2;
       in.szm = bm;
-      if constexpr (TMA) {
-        // Plane s's box: its own +d bonds (colour 1) and the +x / +y bonds
-        // of its -x / -y neighbours (colour 0); -z carried.
-        const float* B = sm.tb[s % NTB];
-        in.jxp = B[1 * TB_ARRAY + tb1];
-        in.jxm = B[0 * TB_ARRAY + tb1 - 1 + (int)p];
-        in.jyp = B[3 * TB_ARRAY + tb1];
-        in.jym = B[2 * TB_ARRAY + tb1 - TB_X];
-        in.jzp = B[5 * TB_ARRAY + tb1];
-      } else {
-        const float(*jb)[R0N] = sm.jb[s & 1];
-        in.jxp = jb[B_XM][b0 + (int)p];
-        in.jxm = jb[B_XP][b0 - 1 + (int)p];
-        in.jyp = jb[B_YM][b0 + R0X];
-        in.jym = jb[B_YP][b0 - R0X];
-        in.jzp = sm.jb[(s + 1) & 1][B_ZM][b0];
-      }
+      const float(*jb)[R0N] = sm.jb[s & 1];
+      in.jxp = jb[B_XM][b0 + (int)p];
+      in.jxm = jb[B_XP][b0 - 1 + (int)p];
+      in.jyp = jb[B_YM][b0 + R0X];
+      in.jym = jb[B_YP][b0 - R0X];
+      in.jzp = sm.jb[(s + 1) & 1][B_ZM][b0];
       in.jzm = jzm1;
       const float4 o = c1s[k0][own1];
       in.s = make_float3(o.x, o.y, o.z);
@@ -541,73 +400,289 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
       const float4 r = site_result<U_OR>(in, 1u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
       dst1[z * plane + off1] = RENORM ? renorm_spin(r) : r;
     }
-    if (s >= 1 && valid1) {
-      if constexpr (TMA)
-        jzm1 = sm.tb[s % NTB][4 * TB_ARRAY + tb1];
-      else
-        jzm1 = sm.jb[s & 1][B_ZP][b0];
-    }
+    if (s >= 1 && valid1) jzm1 = sm.jb[s & 1][B_ZP][b0];
     bm = bc;
     bc = b2;
     cb0 = nb0;
     cs0 = ns0;
-    if constexpr (SL == 2) ns0 = n2s0;
     zs = z1p;
   }
-  if constexpr (TMA) {
-    // A CTA whose wait gave up: its issuing thread waits (bounded) for the
-    // boxes still in flight before the CTA exits.
-    if (t == 0)
-      for (int j = boxes_seen; j < boxes_issued; ++j)
-        if (!mbar_wait_bounded(&sm.bar[j % NTB], (uint32_t)(j / NTB) & 1u, kBoxWaitNs)) break;
+}
+
+// The tensor-box kernel, with one CTA barrier per plane.  Per step s (plane
+// s + 1 for stage 0, plane s for stage 1) a warp
+//   waits (mbarriers) for the colour-1 plane s + 2 and the bond box of plane
+//       s + 1, and (cp.async.wait_group) for its own old spin of plane s + 1;
+//   runs stage 0;
+//   meets the others at the one barrier (stage 0's new colour 0 then visible);
+//   refills the slots that no warp reads any more: colour-1 plane s + 4 (into
+//       plane s's slot), its old colour-0 spin of plane s + 3 (into plane
+//       s - 1's colour-0 slot) and (thread 0) the bond box of plane s + 3 (into
+//       box s - 1's slot) -- each a step and a half ahead of its use;
+//   runs stage 1, reading its own old colour-1 spin of plane s from a
+//       register loaded a step earlier, so that plane s's slot is free once
+//       stage 0 of step s is done everywhere.
+// Colour-1 planes complete on an mbarrier per slot that each thread's
+// cp.async copies arrive on (cp.async.mbarrier.arrive.noinc: all 288
+// threads per plane).  The old colour-0 spin of plane j goes into the slot
+// where stage 0 later writes the site's new value, by the thread that reads
+// it: a thread-private value, so it needs no barrier.  Measured at L = 256:
+// 135.6 us against 142.2 us with the same rings and loads behind two
+// barriers per plane (the second at the top of each step).  Bounded waits:
+// one that gives up sets a.err, the CTA runs to its end, and thread 0 waits
+// (bounded) for its boxes still in flight before it exits.
+template <bool RENORM>
+__global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
+    k_or_sweep_wave(const WaveArgs a, int zc, const __grid_constant__ CUtensorMap bond_map) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  WaveBoxSmem& sm = *reinterpret_cast<WaveBoxSmem*>(smem_raw);
+
+  const int t = threadIdx.x;
+  const int L = a.L, Lh = a.Lh;
+  const uint32_t Lu = (uint32_t)L, Lhu = (uint32_t)Lh;
+  const uint32_t plane = Lu * Lhu;
+  const uint32_t Nh = plane * Lu;
+  const int xh0 = blockIdx.x * WX, y0 = blockIdx.y * WY;
+  const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, L);
+  const int nsteps = z1 - z0 + 2;
+
+  const float4* __restrict__ src0 = a.src;
+  const float4* __restrict__ src1 = a.src + Nh;
+  float4* __restrict__ dst0 = a.dst;
+  float4* __restrict__ dst1 = a.dst + Nh;
+
+  // R1 sites this thread copies in (in-plane offsets).
+  uint32_t l1_off[2];
+  const bool l1_second = t + W_THREADS < R1N;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int i = t + j * W_THREADS;
+    l1_off[j] = (uint32_t)wrap_mod(y0 - 2 + i / R1X, L) * Lhu + (uint32_t)wrap_mod(xh0 - 2 + i % R1X, Lh);
   }
+  // Stage-0 site: R0 position t.
+  const int r0 = t / R0X, cc0 = t % R0X;
+  const uint32_t y_0 = (uint32_t)wrap_mod(y0 - 1 + r0, L), xh_0 = (uint32_t)wrap_mod(xh0 - 1 + cc0, Lh);
+  const bool owned0 = r0 >= 1 && r0 <= WY && cc0 >= 1 && cc0 <= WX && y0 + r0 - 1 < L && xh0 + cc0 - 1 < Lh;
+  const uint32_t off0 = y_0 * Lhu + xh_0;
+  const int b1 = (r0 + 1) * R1X + (cc0 + 1);
+  // Stage-1 site: tile position (t / WX, t % WX).
+  const int r1 = t / WX, cc1 = t % WX;
+  const bool valid1 = t < WX * WY && y0 + r1 < L && xh0 + cc1 < Lh;
+  const uint32_t y_1 = (uint32_t)min(y0 + r1, L - 1), xh_1 = (uint32_t)min(xh0 + cc1, Lh - 1);
+  const uint32_t off1 = y_1 * Lhu + xh_1;
+  const int b0 = (r1 + 1) * R0X + (cc1 + 1);
+  const int own1 = (r1 + 2) * R1X + (cc1 + 2);
+  const int tb0 = (r0 + 1) * TB_X + (cc0 + 1);
+  const int tb1 = (r1 + 2) * TB_X + (cc1 + 2);
+
+  auto z_of = [&](uint32_t zs, uint32_t k) { return zs + k >= Lu ? zs + k - Lu : zs + k; };  // k < L
+  auto load_c1 = [&](int j, uint32_t z) {
+    float4* slot = sm.c1[j % NR];
+    const uint32_t zo = z * plane;
+    cp_async16(&slot[t], src1 + zo + l1_off[0]);
+    if (l1_second) cp_async16(&slot[t + W_THREADS], src1 + zo + l1_off[1]);
+    cp_async_arrive(&sm.full[j % NR]);
+  };
+  auto load_old = [&](int j, uint32_t z) { cp_async16(&sm.c0[j % NR][t], src0 + z * plane + off0); };
+
+  // Bounded waits: one that gives up marks the sweep as failed (a.err) and
+  // stops this thread's further waits (and, for thread 0, its boxes); the
+  // CTA runs to its end, and thread 0 then waits, again bounded, for the
+  // boxes still in flight.
+  bool ok = true;
+  int boxes_issued = 0, boxes_seen = 0;
+  auto give_up = [&] {
+    ok = false;
+    atomicOr(a.err, 1ull);
+  };
+  auto issue_box = [&](int j, uint32_t z) {
+    const int k = j % NR;
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier reads of the slot, then the box
+    mbar_expect_tx(&sm.bar[k], TB_BYTES + a.box_extra_tx);
+    tma_box_4d(sm.tb[k], &bond_map, xh0, y0, (int)z, 0, &sm.bar[k]);
+    boxes_issued = j + 1;
+  };
+  auto wait_box = [&](int j) {
+    if (!ok) return;
+    if (mbar_wait_bounded(&sm.bar[j % NR], (uint32_t)(j / NR) & 1u, kBoxWaitNs))
+      boxes_seen = j + 1;
+    else
+      give_up();
+  };
+  auto wait_c1 = [&](int j) {
+    if (ok && !mbar_wait_bounded(&sm.full[j % NR], (uint32_t)(j / NR) & 1u, kBoxWaitNs)) give_up();
+  };
+
+  uint32_t zs = (uint32_t)wrap_mod(z0 - 2, L);  // plane of j = s
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+      mbar_init(&sm.bar[k], 1);
+      mbar_init(&sm.full[k], W_THREADS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) issue_box(j, z_of(zs, j));
+#pragma unroll
+  for (int j = 0; j < NR; ++j) load_c1(j, z_of(zs, j));  // nsteps + 1 >= 4 > 3
+  load_old(1, z_of(zs, 1));
+  cp_async_commit();
+  load_old(2, z_of(zs, 2));
+  cp_async_commit();
+  wait_c1(0);
+  wait_c1(1);
+  wait_box(0);
+
+  float jzm1 = 0.0f;  // stage 1: the -z bond of this column, from the plane before
+  // Column carries: stage 0's old colour 1 on planes s, s + 1 (a0, a1),
+  // stage 1's new colour 0 on planes s - 1, s (bm, bc), its own old colour 1
+  // on plane s (own).
+  float4 a0 = sm.c1[0][b1], a1 = sm.c1[1][b1], bm = make_float4(0.0f, 0.0f, 0.0f, 0.0f), bc = bm;
+  float4 own = bm;
+  for (int s = 0; s < nsteps; ++s) {
+    const uint32_t z1p = z_of(zs, 1);
+    wait_c1(s + 2);
+    wait_box(s + 1);
+    cp_async_wait<1>();  // this thread's old spin of plane s + 1
+
+    // Stage 0: colour 0 on plane j = s + 1 (stored when s in [1, z1 - z0]).
+    {
+      const uint32_t z = z1p;
+      const uint32_t p = (y_0 + z) & 1u;
+      const float4 a2 = sm.c1[(s + 2) % NR][b1];
+      const float4* p1 = sm.c1[(s + 1) % NR] + b1;
+      const float4 side = p1[p ? 1 : -1];
+      SiteInputs in;
+      in.sxp = p ? side : a1;
+      in.sxm = p ? a1 : side;
+      in.syp = p1[R1X];
+      in.sym = p1[-R1X];
+      in.szp = a2;
+      in.szm = a0;
+      a0 = a1;
+      a1 = a2;
+      const float* B = sm.tb[(s + 1) % NR];
+      in.jxp = B[0 * TB_ARRAY + tb0];
+      in.jxm = B[1 * TB_ARRAY + tb0 - (p ? 0 : 1)];
+      in.jyp = B[2 * TB_ARRAY + tb0];
+      in.jym = B[3 * TB_ARRAY + tb0 - TB_X];
+      in.jzp = B[4 * TB_ARRAY + tb0];
+      in.jzm = sm.tb[s % NR][5 * TB_ARRAY + tb0];
+      float4* slot = &sm.c0[(s + 1) % NR][t];
+      const float4 o = *slot;
+      in.s = make_float3(o.x, o.y, o.z);
+      in.q = 0;
+      in.site = 0;  // over-relaxation draws no random numbers
+      const float4 v = site_result<U_OR>(in, 0u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
+      *slot = v;
+      if (owned0 && s >= 1 && s <= z1 - z0) dst0[z * plane + off0] = RENORM ? renorm_spin(v) : v;
+    }
+    __syncthreads();
+
+    // Refills, each into a slot that no warp reads from here on.
+    if (s + 4 <= nsteps + 1) load_c1(s + 4, z_of(zs, 4));
+    if (s + 3 <= nsteps) load_old(s + 3, z_of(zs, 3));
+    cp_async_commit();
+    if (t == 0 && ok && s + 3 <= nsteps) issue_box(s + 3, z_of(zs, 3));
+
+    // Stage 1: colour 1 on plane j = s, for s >= 2 (bonds as in the
+    // two-barrier kernel's tensor-box path).
+    const float4 b2 = valid1 ? sm.c0[(s + 1) % NR][b0] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (s >= 2 && valid1) {
+      const uint32_t z = zs;
+      const uint32_t p = (1u + y_1 + z) & 1u;
+      const float4* n0 = sm.c0[s % NR] + b0;
+      const float4 side = n0[p ? 1 : -1];
+      SiteInputs in;
+      in.sxp = p ? side : bc;
+      in.sxm = p ? bc : side;
+      in.syp = n0[R0X];
+      in.sym = n0[-R0X];
+      in.szp = b2;
+      in.szm = bm;
+      const float* B = sm.tb[s % NR];
+      in.jxp = B[1 * TB_ARRAY + tb1];
+      in.jxm = B[0 * TB_ARRAY + tb1 - 1 + (int)p];
+      in.jyp = B[3 * TB_ARRAY + tb1];
+      in.jym = B[2 * TB_ARRAY + tb1 - TB_X];
+      in.jzp = B[5 * TB_ARRAY + tb1];
+      in.jzm = jzm1;
+      in.s = make_float3(own.x, own.y, own.z);
+      in.q = 0;
+      in.site = 0;
+      const float4 r = site_result<U_OR>(in, 1u, 0u, 0u, 0u, 0u, 0.0f, 0.0f, 1);
+      dst1[z * plane + off1] = RENORM ? renorm_spin(r) : r;
+    }
+    if (valid1) {
+      own = sm.c1[(s + 1) % NR][own1];  // plane s + 1 (waited for at step s - 1)
+      if (s >= 1) jzm1 = sm.tb[s % NR][4 * TB_ARRAY + tb1];
+    }
+    bm = bc;
+    bc = b2;
+    zs = z1p;
+  }
+  cp_async_wait<0>();
+  if (t == 0)
+    for (int j = boxes_seen; j < boxes_issued; ++j)
+      if (!mbar_wait_bounded(&sm.bar[j % NR], (uint32_t)(j / NR) & 1u, kBoxWaitNs)) break;
 }
 
 // Launch shape, measured at L = 256 (OR sweep time; bit-identical results
 // in every case):
-//  * carveout hint 58 %: the CUDA driver takes the next supported configuration,
-//    164 KB of shared memory -- the smallest that holds three 51 KB CTAs --
-//    and leaves 92 KB of the SM's unified array as L1 for the in-flight bond
-//    loads of stage 0: 166 us.  With 60 KB of L1 left (196 KB shared) 178 us,
-//    with 28 KB 267 us;
+//  * register kernel: carveout hint 58 %: the CUDA driver takes the next
+//    supported configuration, 164 KB of shared memory -- the smallest that
+//    holds three 51 KB CTAs -- and leaves 92 KB of the SM's unified array as
+//    L1 for the in-flight bond loads of stage 0: 166 us.  With 60 KB of L1
+//    left (196 KB shared) 178 us, with 28 KB 267 us;
+//  * tensor-box kernel: its loads do not pass through L1, so the carveout is
+//    the smallest that holds three CTAs (each with the 1 KB the system
+//    reserves), as a percentage of the 228 KB maximum, which the driver
+//    rounds up to a supported configuration (74.3 KB per CTA: 97 % -> 228 KB);
 //  * grid: three CTAs per SM over the tiles (z chunks of L / 3 at L = 256),
 //    one full wave: 166 us; six per SM (two waves) 167 us; two per SM 196 us;
-//    four per SM (a partial second wave) 234 us.
+//    four per SM (a partial second wave) 234 us (register kernel).
 constexpr int W_CARVEOUT_PCT = 58;
-// With tensor-box bonds stage 0's bond loads no longer pass through L1: the
-// carveout is the smallest that holds three CTAs (each with the 1 KB the
-// system reserves), as a percentage of the 228 KB maximum, which the driver
-// rounds up to a supported configuration (74.3 KB per CTA: 97 % -> 228 KB).
-constexpr int W_TMA_CARVEOUT_PCT =
-    (int)((100 * W_MIN_BLOCKS * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472) > 100
+constexpr int W_BOX_CARVEOUT_PCT =
+    (int)((100 * W_MIN_BLOCKS * (sizeof(WaveBoxSmem) + 1024) + 233471) / 233472) > 100
         ? 100
-        : (int)((100 * W_MIN_BLOCKS * (sizeof(WaveTmaSmem) + 1024) + 233471) / 233472);
+        : (int)((100 * W_MIN_BLOCKS * (sizeof(WaveBoxSmem) + 1024) + 233471) / 233472);
+static_assert(W_MIN_BLOCKS * (sizeof(WaveBoxSmem) + 1024) <= 233472, "three tensor-box CTAs per SM");
 constexpr int W_GRID_PER_SM = 3;
 
-// The kernel attributes are per device: applied once on each device used.
-template <bool RENORM, bool TMA>
-cudaError_t configure_wave() {
-  static PerDevice configured;
+// The kernel attributes are per device: set once on each device used.
+template <typename Kernel>
+cudaError_t configure_once(PerDevice& configured, Kernel kernel, size_t smem, int carveout) {
   cudaError_t e = cudaSuccess;
   std::atomic<int>* slot = device_slot(configured, &e);
   if (!slot) return e;
   if (slot->load(std::memory_order_acquire) == 0) {
-    e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM, TMA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)wave_smem<TMA>());
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_or_sweep_wave<RENORM, TMA>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               TMA ? W_TMA_CARVEOUT_PCT : W_CARVEOUT_PCT);
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
     if (e != cudaSuccess) return e;
     slot->store(1, std::memory_order_release);
   }
   return cudaSuccess;
 }
 
-template <bool RENORM, bool TMA>
-cudaError_t launch_wave_as(const WaveArgs& a, dim3 grid, int zc, const CUtensorMap& map, cudaStream_t s) {
-  const cudaError_t e = configure_wave<RENORM, TMA>();
+template <bool RENORM>
+cudaError_t launch_regs(const WaveArgs& a, dim3 grid, int zc, cudaStream_t s) {
+  static PerDevice configured;
+  const cudaError_t e = configure_once(configured, k_or_sweep_wave_regs<RENORM>, sizeof(WaveSmem), W_CARVEOUT_PCT);
   if (e != cudaSuccess) return e;
-  k_or_sweep_wave<RENORM, TMA><<<grid, W_THREADS, wave_smem<TMA>(), s>>>(a, zc, map);
+  k_or_sweep_wave_regs<RENORM><<<grid, W_THREADS, sizeof(WaveSmem), s>>>(a, zc);
+  return cudaGetLastError();
+}
+
+template <bool RENORM>
+cudaError_t launch_boxes(const WaveArgs& a, dim3 grid, int zc, cudaStream_t s) {
+  static PerDevice configured;
+  const cudaError_t e =
+      configure_once(configured, k_or_sweep_wave<RENORM>, sizeof(WaveBoxSmem), W_BOX_CARVEOUT_PCT);
+  if (e != cudaSuccess) return e;
+  k_or_sweep_wave<RENORM><<<grid, W_THREADS, sizeof(WaveBoxSmem), s>>>(a, zc, *a.bond_map);
   return cudaGetLastError();
 }
 
@@ -619,13 +694,8 @@ cudaError_t launch_wave(const WaveArgs& a, int sm_count, cudaStream_t s) {
   if (zc < MIN_ZC) zc = MIN_ZC;
   if (zc > a.L) zc = a.L;
   const dim3 grid(tx, ty, cdiv(a.L, zc));
-  if (a.bond_map) {
-    return a.renorm ? launch_wave_as<true, true>(a, grid, zc, *a.bond_map, s)
-                    : launch_wave_as<false, true>(a, grid, zc, *a.bond_map, s);
-  }
-  static const CUtensorMap unused{};
-  return a.renorm ? launch_wave_as<true, false>(a, grid, zc, unused, s)
-                  : launch_wave_as<false, false>(a, grid, zc, unused, s);
+  if (a.bond_map) return a.renorm ? launch_boxes<true>(a, grid, zc, s) : launch_boxes<false>(a, grid, zc, s);
+  return a.renorm ? launch_regs<true>(a, grid, zc, s) : launch_regs<false>(a, grid, zc, s);
 }
 
 // The padded copy, one warp per padded row (a, z, yp) at a time: the row of

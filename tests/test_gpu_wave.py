@@ -291,3 +291,23 @@ def test_tensor_load_waits_run_out_and_are_reported(hsg):
         ref.set_spins(s0)
         ref.sweep(hsg.schedule(kind=hsg.HSG_NONE, n_or=1, kernel=hsg.HSG_KERNEL_GLOBAL), 1)
         assert np.array_equal(got, ref.spins())
+
+
+def test_register_bonds_when_the_padded_copy_cannot_be_allocated(hsg):
+    """Without memory for the halo-padded couplings (the sweep's second
+    allocation made to fail) the temporally blocked sweep keeps its other
+    kernel, which loads each site's bonds into registers; its results are
+    the global kernel's bit for bit too."""
+    L = 72
+    kw = dict(kind=hsg.HSG_HEATBATH, T=0.7, n_or=2, renorm_every=2, energy_every=1)
+    want = run(hsg, L, kw, 3, hsg.HSG_KERNEL_GLOBAL)
+    with hsg.Lattice(L, 31) as lat:
+        lat.generate_couplings()
+        hsg.hsg_test_fail_alloc(2)  # the first sweep allocates the second spin buffer, then the padded copy
+        try:
+            lat.sweep(hsg.schedule(kernel=hsg.HSG_KERNEL_WAVE, **kw), 3)
+        finally:
+            hsg.hsg_test_fail_alloc(0)
+        got = lat.spins(), lat.energy_log()
+    assert np.array_equal(got[0], want[0])
+    assert np.array_equal(got[1], want[1])
