@@ -39,7 +39,7 @@
 //     box wraps; the colour-1 planes come by cp.async completing on
 //     mbarriers; stage 0's old spins by cp.async into the slot where its new
 //     value goes.  One CTA barrier per plane (the pipeline is described at
-//     the kernel).  135.6 us per sweep at L = 256.
+//     the kernel).  131.5 us per sweep at L = 256.
 //   k_or_sweep_wave_regs (smaller lattices, or no room for the copy): stage
 //     0 loads each site's bonds and old spin into registers a step ahead and
 //     leaves the bonds in shared memory for stage 1; two barriers per plane.
@@ -98,6 +98,12 @@ constexpr uint32_t TB_BYTES = TB_A * TB_ARRAY * 4;         // 8160
 constexpr int TB_SLOT = (TB_BYTES + 127) / 128 * 128 / 4;  // 2048 floats
 constexpr int PAD_X = kPadX, PAD_Y = kPadY;
 constexpr int NR = 4;  // ring depth of every buffer of the tensor-box kernel
+// Warps 7 and 8 have no stage-1 site (WX * WY = 224 = 7 warps): the first
+// thread of warp 7 issues the tensor-box kernel's bond boxes (131.5 us
+// against 131.8 us from thread 0).  Handing them the colour-1 copies as well
+// (six per thread) was slower: 133.8 us.
+constexpr int BOX_ISSUER = WX * WY;
+static_assert(BOX_ISSUER % 32 == 0 && BOX_ISSUER < W_THREADS, "an idle warp issues the boxes");
 struct WaveBoxSmem {
   float4 c1[NR][R1N];  // old colour 1, plane j in slot j % NR
   float4 c0[NR][R0N];  // colour 0 of plane j: its old spins, then its new ones
@@ -105,6 +111,8 @@ struct WaveBoxSmem {
   unsigned long long bar[NR];   // bond boxes
   unsigned long long full[NR];  // colour-1 planes
 };  // 74,304 bytes
+static_assert(R0X == 18 && R0Y == 16 && WX == 16 && WY == 14 && TB_X == 20 && R1X == 20 && W_THREADS == 9 * 32,
+              "the tensor-box kernel's thread-to-site maps assume this tile");
 static_assert(offsetof(WaveBoxSmem, c0) % 128 == 0 && offsetof(WaveBoxSmem, tb) % 128 == 0 &&
                   offsetof(WaveBoxSmem, bar) % 8 == 0,
               "slot alignment");
@@ -417,7 +425,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave_regs(
 //   meets the others at the one barrier (stage 0's new colour 0 then visible);
 //   refills the slots that no warp reads any more: colour-1 plane s + 4 (into
 //       plane s's slot), its old colour-0 spin of plane s + 3 (into plane
-//       s - 1's colour-0 slot) and (thread 0) the bond box of plane s + 3 (into
+//       s - 1's colour-0 slot) and (one thread) the bond box of plane s + 3 (into
 //       box s - 1's slot) -- each a step and a half ahead of its use;
 //   runs stage 1, reading its own old colour-1 spin of plane s from a
 //       register loaded a step earlier, so that plane s's slot is free once
@@ -428,8 +436,11 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS) k_or_sweep_wave_regs(
 // where stage 0 later writes the site's new value, by the thread that reads
 // it: a thread-private value, so it needs no barrier.  Measured at L = 256:
 // 135.6 us against 142.2 us with the same rings and loads behind two
-// barriers per plane (the second at the top of each step).  Bounded waits:
-// one that gives up sets a.err, the CTA runs to its end, and thread 0 waits
+// barriers per plane (the second at the top of each step); 131.8 us once
+// each warp's sites lie in two rows four apart (no bank conflicts on the
+// box and colour-1 reads; the maps are at the kernel's top), 131.5 us with
+// the boxes issued by a warp that has no stage-1 site.  Bounded waits:
+// one that gives up sets a.err, the CTA runs to its end, and the issuing thread waits
 // (bounded) for its boxes still in flight before it exits.
 template <bool RENORM>
 __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
@@ -459,14 +470,32 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     const int i = t + j * W_THREADS;
     l1_off[j] = (uint32_t)wrap_mod(y0 - 2 + i / R1X, L) * Lhu + (uint32_t)wrap_mod(xh0 - 2 + i % R1X, Lh);
   }
-  // Stage-0 site: R0 position t.
-  const int r0 = t / R0X, cc0 = t % R0X;
+  // Stage-0 site: R0 position (r0, cc0) at pos0.  The slots are 20 floats
+  // (bonds) or 20 float4 (colour 1) wide, so a warp that reads two adjacent
+  // rows meets itself in a bank; rows four apart sit 80 floats = 16 banks
+  // apart.  Warps 0-7 therefore take columns 0-15 of two rows four apart
+  // ((0, 4), (1, 5), (2, 6), (3, 7), (8, 12) .. (11, 15)), and warp 8 columns
+  // 16-17 of every row, two columns per quarter-warp row pair.
+  int r0, cc0;
+  if (t < 8 * 32) {
+    const int w = t >> 5, l = t & 31;
+    r0 = (w < 4 ? w : w + 4) + ((l >> 4) << 2);
+    cc0 = l & 15;
+  } else {
+    r0 = (t - 8 * 32) >> 1;
+    cc0 = 16 + (t & 1);
+  }
+  const int pos0 = r0 * R0X + cc0;
   const uint32_t y_0 = (uint32_t)wrap_mod(y0 - 1 + r0, L), xh_0 = (uint32_t)wrap_mod(xh0 - 1 + cc0, Lh);
   const bool owned0 = r0 >= 1 && r0 <= WY && cc0 >= 1 && cc0 <= WX && y0 + r0 - 1 < L && xh0 + cc0 - 1 < Lh;
   const uint32_t off0 = y_0 * Lhu + xh_0;
   const int b1 = (r0 + 1) * R1X + (cc0 + 1);
-  // Stage-1 site: tile position (t / WX, t % WX).
-  const int r1 = t / WX, cc1 = t % WX;
+  // Stage-1 site: tile position (r1, cc1), for t < WX * WY: columns 0-15 of
+  // two rows four apart likewise ((0, 4) .. (3, 7), (8, 12), (9, 13); the
+  // last warp (10, 11)).
+  const int w1 = t >> 5, hi1 = (t >> 4) & 1;
+  const int ra = w1 < 4 ? w1 : (w1 < 6 ? w1 + 4 : 10);
+  const int r1 = t < WX * WY ? (hi1 ? (w1 < 6 ? ra + 4 : 11) : ra) : 0, cc1 = t & 15;
   const bool valid1 = t < WX * WY && y0 + r1 < L && xh0 + cc1 < Lh;
   const uint32_t y_1 = (uint32_t)min(y0 + r1, L - 1), xh_1 = (uint32_t)min(xh0 + cc1, Lh - 1);
   const uint32_t off1 = y_1 * Lhu + xh_1;
@@ -483,11 +512,11 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     if (l1_second) cp_async16(&slot[t + W_THREADS], src1 + zo + l1_off[1]);
     cp_async_arrive(&sm.full[j % NR]);
   };
-  auto load_old = [&](int j, uint32_t z) { cp_async16(&sm.c0[j % NR][t], src0 + z * plane + off0); };
+  auto load_old = [&](int j, uint32_t z) { cp_async16(&sm.c0[j % NR][pos0], src0 + z * plane + off0); };
 
   // Bounded waits: one that gives up marks the sweep as failed (a.err) and
-  // stops this thread's further waits (and, for thread 0, its boxes); the
-  // CTA runs to its end, and thread 0 then waits, again bounded, for the
+  // stops this thread's further waits (and, for BOX_ISSUER, its boxes); the
+  // CTA runs to its end, and BOX_ISSUER then waits, again bounded, for the
   // boxes still in flight.
   bool ok = true;
   int boxes_issued = 0, boxes_seen = 0;
@@ -523,7 +552,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  if (t == 0)
+  if (t == BOX_ISSUER)
 #pragma unroll
     for (int j = 0; j < 3; ++j) issue_box(j, z_of(zs, j));
 #pragma unroll
@@ -571,7 +600,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
       in.jym = B[3 * TB_ARRAY + tb0 - TB_X];
       in.jzp = B[4 * TB_ARRAY + tb0];
       in.jzm = sm.tb[s % NR][5 * TB_ARRAY + tb0];
-      float4* slot = &sm.c0[(s + 1) % NR][t];
+      float4* slot = &sm.c0[(s + 1) % NR][pos0];
       const float4 o = *slot;
       in.s = make_float3(o.x, o.y, o.z);
       in.q = 0;
@@ -586,7 +615,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     if (s + 4 <= nsteps + 1) load_c1(s + 4, z_of(zs, 4));
     if (s + 3 <= nsteps) load_old(s + 3, z_of(zs, 3));
     cp_async_commit();
-    if (t == 0 && ok && s + 3 <= nsteps) issue_box(s + 3, z_of(zs, 3));
+    if (t == BOX_ISSUER && ok && s + 3 <= nsteps) issue_box(s + 3, z_of(zs, 3));
 
     // Stage 1: colour 1 on plane j = s, for s >= 2 (bonds as in the
     // two-barrier kernel's tensor-box path).
@@ -625,7 +654,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
     zs = z1p;
   }
   cp_async_wait<0>();
-  if (t == 0)
+  if (t == BOX_ISSUER)
     for (int j = boxes_seen; j < boxes_issued; ++j)
       if (!mbar_wait_bounded(&sm.bar[j % NR], (uint32_t)(j / NR) & 1u, kBoxWaitNs)) break;
 }
