@@ -293,7 +293,7 @@ hsg_status run_half_sweep(hsg_ctx* c, const hsg_schedule* s, int update, int col
   const hsg::SweepArgs a = sweep_args(c, colour, beta_of(s->T), s->step, s->hits);
   int variant = pick_variant(c, s->kernel);
   if (variant == hsg::V_WAVE) variant = hsg::V_GLOBAL;  // a single colour: the plain kernel
-  return launch(c, kclass, 1, "half-sweep kernel", [&] { return hsg::launch_half_sweep(upd, variant, a, c->stream); });
+  return launch(c, kclass, 1, "half-sweep kernel", [&] { return hsg::launch_half_sweep(upd, variant, a, c->sm_count, c->stream); });
 }
 
 // Both colours of one over-relaxation sweep in one temporally blocked launch

@@ -137,6 +137,11 @@ __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t
 // 1/|h| is rsqrtf (2 ulp); the azimuth uses the fast sine/cosine on
 // (-pi, pi) (absolute error ~4e-7); divisions by numbers in [1e-6, 2] use
 // the fast divide (2 ulp).  Every one of these errors is below 1e-6.
+// (Gathering ct n + c1 e1 + c2 e2 into fewer operations -- ct n + (c1, s c2,
+// 0) + a D (nx, ny, 0) - (0, 0, D), D = s c1 nx + c2 ny -- executed 3.4 %
+// fewer instructions in the L = 256 column kernel but took 98.9 us against
+// 93.7 us: its loads were scheduled worse, long-scoreboard stalls 8.1
+// against 4.8 per issue.)
 __device__ __forceinline__ float3 update_heatbath(float3 h, uint32_t site, uint32_t colour, uint32_t sweep_lo,
                                                   uint32_t sweep_hi, uint32_t k0, uint32_t k1, float beta) {
   const uint4 r = philox4x32_10(make_uint4(site, sweep_lo, (KIND_HB << 24) | (colour << 16), sweep_hi), k0, k1);

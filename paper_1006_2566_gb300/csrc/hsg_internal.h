@@ -92,8 +92,9 @@ struct SweepArgs {
 enum Variant : int { V_AUTO = 0, V_GLOBAL = 1, V_SLAB = 2, V_WAVE = 3 };
 
 // Half-sweep of update kind `upd` (UpdKind) with kernel `variant`
-// (V_GLOBAL or V_SLAB).  One kernel launch.
-cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, cudaStream_t s);
+// (V_GLOBAL or V_SLAB).  One kernel launch; `sm_count` (the device's SMs)
+// shapes the slab kernel's grid.
+cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, int sm_count, cudaStream_t s);
 
 // Arguments of one temporally blocked over-relaxation sweep (hsg_wave.cu):
 // colour 0 then colour 1, read from `src` and written to `dst`.

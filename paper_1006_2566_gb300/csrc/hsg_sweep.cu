@@ -8,7 +8,7 @@
 //            L1/L2 (the lattice is streamed once per half-sweep from HBM).
 //            Its heat-bath launches march a thread up a short column of
 //            planes instead (k_half_sweep_column).
-//   slab   : a CTA owns a (32 xh) x (8 y) column tile and marches up a chunk
+//   slab   : a CTA owns a (32 xh) x (4 y) column tile and marches up a chunk
 //            of z planes.  The other colour's plane z (with a one-site halo)
 //            is staged in shared memory for the x and y neighbours; planes
 //            z-1 and z+1 stay in registers, so each other-colour spin is
@@ -155,27 +155,42 @@ __global__ void __launch_bounds__(G_THREADS, (U == U_OR || U == U_HB) ? 16 : 1)
 }
 
 // ---------------------------------------------------------------------------
-// Slab variant.
+// Slab variant.  A CTA of TX x SLAB_TY threads owns a column tile of the
+// updated colour and marches up zc planes; zc is chosen at launch so that
+// the grid holds SLAB_CTAS_PER_SM CTAs per SM (at L = 128: 7 planes, 1216
+// CTAs; from L = 256 the cap of 16 planes).  Indices are 32-bit: every
+// offset is below N/2 < 2^31.  Registers are held to what 10 (over-
+// relaxation) or 8 (the others) resident CTAs allow.  Measured on GB300
+// (bit-identical throughout): the L = 128 4-hit Metropolis + OR workload
+// 15.0 us (OR) and 34.0 us (Metropolis) per half-sweep against 26.0 and
+// 45.3 us with 32 x 8 tiles of 16 planes, 64-bit indices and no register
+// bound; the L = 256 OR half-sweep 144 us against 162 us.
 // ---------------------------------------------------------------------------
-constexpr int TX = 32, TY = 8, ZC = 16;
+constexpr int TX = 32, SLAB_TY = 4, SLAB_ZC_MAX = 16, SLAB_CTAS_PER_SM = 8;
+template <int U>
+constexpr int slab_min_blocks() {
+  return U == U_OR ? 10 : 8;
+}
 
 template <int U>
-__global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
+__global__ void __launch_bounds__(TX* SLAB_TY, slab_min_blocks<U>()) k_half_sweep_slab(const SweepArgs a, int zc) {
+  constexpr int TY = SLAB_TY;
   // Two buffers of the other colour's plane tile: slot (r, c) holds the site
   // ((x0 + c - 1) mod Lh, (y0 + r - 1) mod L); the corners are unused.
   __shared__ float4 plane[2][TY + 2][TX + 2];
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int L = a.L, Lh = a.Lh;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * ZC;
-  const int z1 = min(z0 + ZC, L);
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, L);
   const int xh = x0 + tx, y = y0 + ty;
   const bool valid = xh < Lh && y < L;
   // Threads past the lattice edge fill their slot with the periodic image.
-  const int xw = xh % Lh, yw = y % L;
-  const int x_left = (x0 + Lh - 1) % Lh, x_right = (x0 + TX) % Lh;
-  const int y_top = (y0 + L - 1) % L, y_bot = (y0 + TY) % L;
-  const long long plane_sz = (long long)L * Lh;
-  const long long col = (long long)yw * Lh + xw;  // this slot's offset in a plane
+  const uint32_t xw = (uint32_t)(xh % Lh), yw = (uint32_t)(y % L);
+  const uint32_t x_left = (uint32_t)((x0 + Lh - 1) % Lh), x_right = (uint32_t)((x0 + TX) % Lh);
+  const uint32_t y_top = (uint32_t)((y0 + L - 1) % L), y_bot = (uint32_t)((y0 + TY) % L);
+  const uint32_t Lhu = (uint32_t)Lh;
+  const uint32_t plane_sz = (uint32_t)L * Lhu;
+  const uint32_t col = yw * Lhu + xw;  // this slot's offset in a plane
   uint32_t sweep_lo = a.sweep_lo, sweep_hi = a.sweep_hi;
   if constexpr (U != U_OR) {
     if (a.sweep_ptr) {
@@ -185,29 +200,29 @@ __global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
     }
   }
 
-  int zprev = wrap_dec(z0, L);
+  const uint32_t zprev = (uint32_t)wrap_dec(z0, L);
   float4 s_zm = __ldg(a.oth + zprev * plane_sz + col);
-  float4 s_z = __ldg(a.oth + z0 * plane_sz + col);
+  float4 s_z = __ldg(a.oth + (uint32_t)z0 * plane_sz + col);
   float jzm = valid ? __ldg(a.jz_oth + zprev * plane_sz + col) : 0.0f;
 
   for (int z = z0; z < z1; ++z) {
-    const int zn = wrap_inc(z, L);
+    const uint32_t zn = (uint32_t)wrap_inc(z, L);
     const float4 s_zp = __ldg(a.oth + zn * plane_sz + col);
-    const long long pz = (long long)z * plane_sz;
+    const uint32_t pz = (uint32_t)z * plane_sz;
     float4(*buf)[TX + 2] = plane[(z - z0) & 1];
     buf[ty + 1][tx + 1] = s_z;
-    if (ty == 0) buf[0][tx + 1] = __ldg(a.oth + pz + (long long)y_top * Lh + xw);
-    if (ty == 1) buf[TY + 1][tx + 1] = __ldg(a.oth + pz + (long long)y_bot * Lh + xw);
-    if (tx == 0) buf[ty + 1][0] = __ldg(a.oth + pz + (long long)yw * Lh + x_left);
-    if (tx == 1) buf[ty + 1][TX + 1] = __ldg(a.oth + pz + (long long)yw * Lh + x_right);
+    if (ty == 0) buf[0][tx + 1] = __ldg(a.oth + pz + y_top * Lhu + xw);
+    if (ty == 1) buf[TY + 1][tx + 1] = __ldg(a.oth + pz + y_bot * Lhu + xw);
+    if (tx == 0) buf[ty + 1][0] = __ldg(a.oth + pz + yw * Lhu + x_left);
+    if (tx == 1) buf[ty + 1][TX + 1] = __ldg(a.oth + pz + yw * Lhu + x_right);
     __syncthreads();
     if (valid) {
       const int p = (a.colour + y + z) & 1;
-      const long long row = pz + (long long)y * Lh;
-      const long long q = row + xh;
+      const uint32_t row = pz + (uint32_t)y * Lhu;
+      const uint32_t q = row + (uint32_t)xh;
       const float jxp = __ldg(a.jx_own + q), jyp = __ldg(a.jy_own + q), jzp = __ldg(a.jz_own + q);
-      const float jxm = __ldg(a.jx_oth + row + (p ? xh : wrap_dec(xh, Lh)));
-      const float jym = __ldg(a.jy_oth + pz + (long long)wrap_dec(y, L) * Lh + xh);
+      const float jxm = __ldg(a.jx_oth + row + (uint32_t)(p ? xh : wrap_dec(xh, Lh)));
+      const float jym = __ldg(a.jy_oth + pz + (uint32_t)wrap_dec(y, L) * Lhu + (uint32_t)xh);
       const float jz_here = __ldg(a.jz_oth + q);  // -z bond of the site above
       float3 s = make_float3(0.0f, 0.0f, 0.0f);
       if constexpr (U != U_HB) {
@@ -226,15 +241,27 @@ __global__ void __launch_bounds__(TX* TY) k_half_sweep_slab(const SweepArgs a) {
   }
 }
 
+// Planes per slab CTA: the grid holds SLAB_CTAS_PER_SM CTAs per SM where
+// the lattice allows, at most SLAB_ZC_MAX planes each.
+int slab_zc(int L, unsigned tiles, int sm_count) {
+  const long long want = (long long)SLAB_CTAS_PER_SM * (sm_count > 0 ? sm_count : 1);
+  long long chunks = (want + tiles - 1) / tiles;
+  if (chunks < 1) chunks = 1;
+  int zc = (int)((L + chunks - 1) / chunks);
+  return zc < 1 ? 1 : (zc > SLAB_ZC_MAX ? SLAB_ZC_MAX : zc);
+}
+
 template <int U>
-cudaError_t launch_kind(int variant, const SweepArgs& a, cudaStream_t s) {
+cudaError_t launch_kind(int variant, const SweepArgs& a, int sm_count, cudaStream_t s) {
   if (a.packed) {
     const dim3 block = a.Lh >= 64 ? dim3(64, 2) : dim3(32, 4);
     const dim3 grid(cdiv(a.Lh, block.x), cdiv(a.L, block.y), (unsigned)a.L);
     k_half_sweep_global_packed<U><<<grid, block, 0, s>>>(a);
   } else if (variant == V_SLAB) {
-    const dim3 grid(cdiv(a.Lh, TX), cdiv(a.L, TY), cdiv(a.L, ZC));
-    k_half_sweep_slab<U><<<grid, dim3(TX, TY), 0, s>>>(a);
+    const unsigned tx = cdiv(a.Lh, TX), ty = cdiv(a.L, SLAB_TY);
+    const int zc = slab_zc(a.L, tx * ty, sm_count);
+    const dim3 grid(tx, ty, cdiv(a.L, zc));
+    k_half_sweep_slab<U><<<grid, dim3(TX, SLAB_TY), 0, s>>>(a, zc);
   } else {
     const dim3 block = a.Lh >= 64 ? dim3(64, 2) : dim3(32, 4);
     const dim3 grid(cdiv(a.Lh, block.x), cdiv(a.L, block.y), (unsigned)a.L);
@@ -250,14 +277,14 @@ cudaError_t launch_kind(int variant, const SweepArgs& a, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, cudaStream_t s) {
+cudaError_t launch_half_sweep(int upd, int variant, const SweepArgs& a, int sm_count, cudaStream_t s) {
   switch (upd) {
-    case U_OR: return launch_kind<U_OR>(variant, a, s);
-    case U_MET_SPHERE: return launch_kind<U_MET_SPHERE>(variant, a, s);
-    case U_MET_BALL: return launch_kind<U_MET_BALL>(variant, a, s);
-    case U_HB: return launch_kind<U_HB>(variant, a, s);
-    case U_MET_OR_SPHERE: return launch_kind<U_MET_OR_SPHERE>(variant, a, s);
-    case U_MET_OR_BALL: return launch_kind<U_MET_OR_BALL>(variant, a, s);
+    case U_OR: return launch_kind<U_OR>(variant, a, sm_count, s);
+    case U_MET_SPHERE: return launch_kind<U_MET_SPHERE>(variant, a, sm_count, s);
+    case U_MET_BALL: return launch_kind<U_MET_BALL>(variant, a, sm_count, s);
+    case U_HB: return launch_kind<U_HB>(variant, a, sm_count, s);
+    case U_MET_OR_SPHERE: return launch_kind<U_MET_OR_SPHERE>(variant, a, sm_count, s);
+    case U_MET_OR_BALL: return launch_kind<U_MET_OR_BALL>(variant, a, sm_count, s);
     default: return cudaErrorInvalidValue;
   }
 }
