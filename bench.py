@@ -404,7 +404,11 @@ def run_ours(args, wl):
     # and the spins).  Two lattices on two streams take alternate steps, so
     # one step's copies overlap the other's sweeps (copy engines and SMs
     # work at once); each step still waits for its own uploads before its
-    # sweeps and for its sweeps before its read-back.
+    # sweeps and for its sweeps before its read-back.  The sweeps of the two
+    # lattices are chained by an event (a step's sweeps start once the
+    # previous step's have ended): run side by side, the two lattices'
+    # kernels share the SMs and break the temporally blocked sweep's single
+    # wave of CTAs (7.98 against 7.81 ms per step).
     e2e = None
     if not args.no_e2e:
         Jh = torch.from_numpy(J).pin_memory()
@@ -415,11 +419,18 @@ def run_ours(args, wl):
         lat2 = hsg.Lattice(L, wl["seed"], sample, 0, stream2,
                            layout=hsg.HSG_LAYOUT_PACKED if packed else hsg.HSG_LAYOUT_FLOAT4)
         pair = [lat, lat2]
+        streams = {id(lat): stream, id(lat2): stream2}
+        swept = [None]  # event after the last step's sweeps
 
         def begin(lt):
             lt.set_couplings(Jh)  # H2D 12N bytes, returns when copied
             lt.set_spins(s_in)  # H2D 12N bytes, returns when copied
+            st = streams[id(lt)]
+            if swept[0] is not None:
+                st.wait_event(swept[0])
             lt.sweep(sched, sps)  # queued on the lattice's stream
+            swept[0] = torch.cuda.Event()
+            swept[0].record(st)
 
         def finish(lt, out):
             lt.energy()  # waits for the sweeps; D2H 8 bytes
@@ -448,7 +459,7 @@ def run_ours(args, wl):
                "h2d_bytes_per_step": int(Jh.numel() * 4 + s_in.numel() * 4),
                "d2h_bytes_per_step": int(8 + outs[0].numel() * 4), "ms_per_step": round(e2e_ms / args.steps, 4),
                "pipelined": "two lattices on two streams take alternate steps; one step's host copies overlap "
-                            "the other's sweeps"}
+                            "the other's sweeps, and each step's sweeps start after the previous step's"}
     lat.close()
     if world > 1:
         torch.distributed.barrier()
