@@ -59,9 +59,10 @@ WORKLOADS = {
               "FP64 energy every 10 sweeps; 1 step = 10 sweeps")),
     "l16_met": dict(
         L=16, seed=1, kind="MET", T=1.0, n_or=0, hits=1, proposal="SPHERE", step=0.5, renorm_every=0,
-        energy_every=10, sweeps_per_step=10,
-        desc=("L=16 periodic 3D Heisenberg spin glass, 1 sample, Gaussian J; checkerboard Metropolis 1 hit, "
-              "uniform-sphere proposal, T=1.0; E/N every 10 sweeps; 1 step = 10 sweeps")),
+        energy_every=10, sweeps_per_step=10, j_fp64=True,
+        desc=("L=16 periodic 3D Heisenberg spin glass, 1 sample, Gaussian J in fp64 (rounded to fp32 on upload); "
+              "checkerboard Metropolis 1 hit, uniform-sphere proposal, T=1.0; E/N every 10 sweeps; "
+              "1 step = 10 sweeps")),
     "l128_metor_fused": dict(
         L=128, seed=2, kind="METOR", T=0.5, n_or=0, hits=4, proposal="BALL", step=0.5, renorm_every=10,
         energy_every=10, sweeps_per_step=10,
@@ -342,7 +343,10 @@ def run_ours(args, wl):
     sps = wl["sweeps_per_step"]
     stream = torch.cuda.Stream()
     sample = hdist.rank_sample(rank)  # weak scaling: one disorder sample per rank
-    J = inputs.gaussian_couplings(L, seed=wl["seed"], sample=sample, dtype=np.float32)
+    # fp64 couplings where the workload specifies them (the library rounds
+    # them to fp32 on upload), fp32 otherwise
+    J = inputs.gaussian_couplings(L, seed=wl["seed"], sample=sample,
+                                  dtype=np.float64 if wl.get("j_fp64") else np.float32)
     packed = args.layout == "packed"
     lat = hsg.Lattice(L, wl["seed"], sample, 0, stream,
                       layout=hsg.HSG_LAYOUT_PACKED if packed else hsg.HSG_LAYOUT_FLOAT4)
@@ -456,7 +460,7 @@ def run_ours(args, wl):
         e2e_ms = hdist.max_over_ranks(e2e_ms, device="cuda")
         lat2.close()
         e2e = {"value": round(world * step_units(wl) * args.steps / (e2e_ms * 1e6), 4), "unit": "spin updates/ns",
-               "h2d_bytes_per_step": int(Jh.numel() * 4 + s_in.numel() * 4),
+               "h2d_bytes_per_step": int(Jh.numel() * Jh.element_size() + s_in.numel() * 4),
                "d2h_bytes_per_step": int(8 + outs[0].numel() * 4), "ms_per_step": round(e2e_ms / args.steps, 4),
                "pipelined": "two lattices on two streams take alternate steps; one step's host copies overlap "
                             "the other's sweeps, and each step's sweeps start after the previous step's"}
@@ -655,19 +659,22 @@ def _site_errors(oracle, L, J, before, after, sites, upd, colour, p):
             "max_err_over_kappa": round(max(over_kappa), 3)}
 
 
-def errors_vs_oracle(hsg, lat, J32, wl, e_last):
+def errors_vs_oracle(hsg, lat, J_in, wl, e_last):
     """The error of each reported quantity against the FP64 oracle, measured
     after the timed region on the benchmark's own lattice (the oracle leg):
     the logged E/N against the oracle's energy of the same spins; one
     main-update half-sweep (colour 0) and one over-relaxation sweep of the
     kernel the benchmark times (colour 0 from the state before it, colour 1
     from the GPU's own new colour 0) at >= 3000 sampled sites per layer; and
-    the FP64 renormalisation of the whole lattice against the oracle's."""
+    the FP64 renormalisation of the whole lattice against the oracle's.
+    The oracle is fed the couplings the lattice holds (the input rounded to
+    fp32); with fp64 input, what that rounding alone changes in E/N is
+    reported apart."""
     import oracle
 
     oracle.build()
     L, N = wl["L"], wl["L"] ** 3
-    J = J32.astype(np.float64)
+    J = np.asarray(J_in, dtype=np.float32).astype(np.float64)
     rng = np.random.default_rng(7)
     out = {"rules": "max |diff| per spin component at each sampled site; heat-bath frame-branch band and "
                     "Metropolis near-threshold sites excluded; ill-conditioned = 4 kappa > 1e-5, kappa = "
@@ -676,6 +683,10 @@ def errors_vs_oracle(hsg, lat, J32, wl, e_last):
     if wl["energy_every"]:
         e_ref = oracle.energy(L, J, s_end) / N
         out["energy_per_spin"] = {"gpu": e_last, "oracle": e_ref, "abs_err": abs(e_last - e_ref)}
+    if np.asarray(J_in).dtype == np.float64:
+        e_raw = oracle.energy(L, np.asarray(J_in), s_end) / N
+        out["fp64_coupling_rounding"] = {"energy_per_spin_raw_fp64_J": e_raw,
+                                         "abs_diff_vs_rounded_J": abs(e_raw - oracle.energy(L, J, s_end) / N)}
     # FP64 renormalisation of the current state against the oracle's
     lat.renorm()
     got = lat.spins().astype(np.float64)

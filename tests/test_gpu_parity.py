@@ -491,6 +491,47 @@ def test_metropolis_sweeps_layer_by_layer(hsg, kind):
                                                          proposal=1), f"{kind}+OR sweeps L={L}")
 
 
+def test_l16_workload_with_fp64_couplings_and_their_rounding_error(hsg):
+    """The L = 16 workload as specified: fp64 couplings (rounded to fp32 on
+    upload), 1-hit Metropolis with the uniform-sphere proposal at T = 1,
+    10 sweeps.  Every layer against the oracle fed the same rounded
+    couplings (the parity bar), and, separately, what the rounding alone
+    changes: the oracle's layer with the raw fp64 couplings against its
+    layer with the rounded ones, from the same state.  An accepted proposal
+    does not depend on J, so the rounding can only flip decisions whose
+    margin it crosses: at most 0.2 % of a colour's sites per layer (none is
+    expected).  E/N of the final state with raw against rounded couplings is
+    recorded too."""
+    L, T = 16, 1.0
+    J = inputs.gaussian_couplings(L, seed=1)
+    Jr = inputs.round_to_f32(J)
+    assert not np.array_equal(J, Jr)
+    sched = hsg.schedule(kind=hsg.HSG_METROPOLIS, hits=1, proposal=hsg.HSG_PROP_SPHERE, T=T)
+    with hsg.Lattice(L, 1) as lat:
+        lat.set_couplings(J)
+        layers, _ = layered_run(hsg, lat, sched, hsg.HSG_METROPOLIS, 0, 10, 0, 0)
+        final = lat.spins()
+    assert len(layers) == 20
+    params_of = lambda sw: oracle.Params(key=oracle.key(1), sweep=sw, beta=1.0 / T, hits=1,  # noqa: E731
+                                         proposal=hsg.HSG_PROP_SPHERE)
+    check_layers(L, Jr, layers, params_of, "L=16 fp64-J Metropolis")
+    worst_flips, worst_diff = 0, 0.0
+    for (upd, c, sw), before, _ in layers:
+        with_raw = before.astype(np.float64)
+        with_rounded = with_raw.copy()
+        oracle.half_sweep(L, J, with_raw, oracle.MET, c, params_of(sw))
+        oracle.half_sweep(L, Jr, with_rounded, oracle.MET, c, params_of(sw))
+        diff = np.max(np.abs(with_raw - with_rounded).reshape(-1, 3), axis=1)
+        flips = int(np.sum(diff > 1e-5))
+        assert flips <= max(2, 0.002 * L ** 3 // 2), (sw, c, flips)
+        worst_flips, worst_diff = max(worst_flips, flips), max(worst_diff, float(diff.max()))
+    e_raw = oracle.energy(L, J, final.astype(np.float64)) / L ** 3
+    e_rounded = oracle.energy(L, Jr, final.astype(np.float64)) / L ** 3
+    record(label="L=16 fp64-J rounding to fp32 (oracle raw vs rounded, per layer)", L=L,
+           decision_flips_max=worst_flips, max_abs_diff=worst_diff, energy_per_spin_diff=abs(e_raw - e_rounded))
+    assert abs(e_raw - e_rounded) < 1e-6
+
+
 def test_long_run_energy_statistics_match_oracle(hsg):
     """L = 16, Gaussian J, Metropolis 1 hit (sphere), T = 1: the mean E/N of
     1500 sweeps agrees with the oracle's within 3 sigma."""
