@@ -423,13 +423,15 @@ const char* hsg_pool_last_error(const hsg_pool* pool);
 hsg_status hsg_test_fail_alloc(int k);
 
 /*
- * Fault injection for tests of the bounded waits: with on != 0, every
- * temporally blocked sweep launched from now waits for more bytes than each
- * of its couplings' tensor loads delivers, so that every such wait runs out
- * (after 0.2 s; nothing hangs, nothing faults), the sweep's spins are not
- * valid, and the next hsg_energy on the context returns HSG_ETIMEOUT (once).
- * on = 0 restores.  Process-wide; a sweep captured in a CUDA graph keeps the
- * setting it was captured with.  Library-specific.
+ * Fault injection for tests of the bounded waits of the temporally blocked
+ * sweep's tensor-box kernel (L >= 32).  Bit 0 of `on`: every sweep launched
+ * from now waits for more bytes than each of its couplings' tensor loads
+ * delivers; bit 1: for one arrival more than the copies of each of its
+ * colour-1 planes make.  Every such wait runs out (after 0.2 s; nothing
+ * hangs, nothing faults), the sweep's spins are not valid, and the next
+ * hsg_energy on the context returns HSG_ETIMEOUT (once).  on = 0 restores;
+ * HSG_EINVAL outside 0 .. 3.  Process-wide; a sweep captured in a CUDA
+ * graph keeps the setting it was captured with.  Library-specific.
  */
 hsg_status hsg_test_stall_tensor_loads(int on);
 

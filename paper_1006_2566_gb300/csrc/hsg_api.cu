@@ -309,7 +309,9 @@ hsg_status run_or_sweep_wave(hsg_ctx* c, bool renorm) {
   a.renorm = renorm;
   a.bond_map = c->use_tma ? &c->bond_map : nullptr;
   a.err = c->d_ctr + 2;
-  a.box_extra_tx = g_test_stall_boxes.load() ? 16u : 0u;
+  const int stall = g_test_stall_boxes.load();
+  a.box_extra_tx = (stall & 1) ? 16u : 0u;
+  a.c1_extra_arrivals = (stall & 2) ? 1u : 0u;
   hsg_status st = launch(c, renorm ? HSG_PROF_OVERRELAX_RENORM : HSG_PROF_OVERRELAX, 1, "over-relaxation sweep kernel",
                          [&] { return hsg::launch_or_sweep_wave(a, c->sm_count, c->stream); });
   if (st == HSG_OK) std::swap(c->spins, c->spins_alt);
@@ -961,7 +963,8 @@ hsg_status hsg_philox(uint64_t seed, uint32_t sample, uint32_t replica, uint32_t
 }
 
 hsg_status hsg_test_stall_tensor_loads(int on) {
-  g_test_stall_boxes.store(on != 0 ? 1 : 0);
+  if (on < 0 || on > 3) return fail(nullptr, HSG_EINVAL, "on must be 0 .. 3");
+  g_test_stall_boxes.store(on);
   return HSG_OK;
 }
 

@@ -113,6 +113,9 @@ struct WaveArgs {
   // Bytes each box's wait expects beyond the box (0; > 0 only to test the
   // bounded waits: the waits then cannot complete and run out).
   uint32_t box_extra_tx;
+  // Arrivals each colour-1 plane's barrier expects beyond its copies (0;
+  // 1 only to test the bounded waits, likewise).
+  uint32_t c1_extra_arrivals;
 };
 
 // Over-relaxation sweep (both colours) in one launch, bit-identical to the

@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(W_THREADS, W_MIN_BLOCKS)
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
       mbar_init(&sm.bar[k], 1);
-      mbar_init(&sm.full[k], W_THREADS);
+      mbar_init(&sm.full[k], W_THREADS + a.c1_extra_arrivals);
     }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }

@@ -314,8 +314,9 @@ def hsg_test_fail_alloc(k: int) -> None:
     _check(_lib.hsg_test_fail_alloc(int(k)))
 
 
-def hsg_test_stall_tensor_loads(on: bool) -> None:
-    _check(_lib.hsg_test_stall_tensor_loads(1 if on else 0))
+def hsg_test_stall_tensor_loads(on) -> None:
+    """True / 1: the couplings' tensor loads; 2: the colour-1 planes' barriers; 3: both; False / 0: off."""
+    _check(_lib.hsg_test_stall_tensor_loads(int(on)))
 
 
 def hsg_energy_noalloc(L: int, spins, J, e_out, stream=None) -> None:

@@ -76,6 +76,9 @@ def test_host_side_argument_checks(lib):
         assert hsg._lib.hsg_philox(1, sample, replica, 0, 0, 0, 4, out, None) == hsg.HSG_EINVAL
     assert hsg._lib.hsg_test_fail_alloc(-1) == hsg.HSG_EINVAL
     assert hsg._lib.hsg_test_fail_alloc(0) == hsg.HSG_OK
+    assert hsg._lib.hsg_test_stall_tensor_loads(4) == hsg.HSG_EINVAL
+    assert hsg._lib.hsg_test_stall_tensor_loads(-1) == hsg.HSG_EINVAL
+    assert hsg._lib.hsg_test_stall_tensor_loads(0) == hsg.HSG_OK
     # NULL / misaligned outputs are refused before any launch
     assert hsg._lib.hsg_philox(1, 0, 0, 0, 0, 0, 4, None, None) == hsg.HSG_EINVAL
     assert hsg._lib.hsg_philox(1, 0, 0, 0, 0, 0, 4, ctypes.c_void_p(8), None) == hsg.HSG_EINVAL

@@ -255,10 +255,12 @@ def test_new_couplings_after_wave_sweeps(hsg, source):
     assert np.array_equal(outs[0][0], outs[1][0])
 
 
-def test_tensor_load_waits_run_out_and_are_reported(hsg):
-    """The waits of the temporally blocked sweep for its couplings' tensor
-    loads are bounded (0.2 s).  With the test switch each wait expects more
-    bytes than its load delivers, so every wait runs out: the sweep still
+@pytest.mark.parametrize("which", [1, 2, 3])
+def test_tensor_load_waits_run_out_and_are_reported(hsg, which):
+    """The waits of the temporally blocked sweep for its loads are bounded
+    (0.2 s): for the couplings' tensor boxes (which = 1), for the colour-1
+    planes' barriers (2), or both (3).  With the test switch each such wait
+    expects more than its loads deliver, so it runs out: the sweep still
     ends, hsg_energy reports HSG_ETIMEOUT (once), and the context stays
     usable -- with the switch off, the same sweep from the same state equals
     the global kernel's bit for bit."""
@@ -272,7 +274,7 @@ def test_tensor_load_waits_run_out_and_are_reported(hsg):
         lat.sweep(sched, 1)  # makes the padded copy: tensor loads from here on
         lat.energy()
         s0 = lat.spins()
-        hsg.hsg_test_stall_tensor_loads(True)
+        hsg.hsg_test_stall_tensor_loads(which)
         try:
             t0 = time.perf_counter()
             lat.sweep(sched, 1)
