@@ -78,8 +78,9 @@ enum { HSG_HOST = 0, HSG_DEVICE = 1 };
 /* Half-sweep kernel variant. */
 enum {
   HSG_KERNEL_AUTO = 0,   /* library's choice: HSG_KERNEL_WAVE when the lattice's
-                          * spins and bonds (28 N bytes) exceed the device's L2,
-                          * so that the sweep streams from HBM; else GLOBAL */
+                          * spins and bonds (28 N bytes) exceed three quarters of
+                          * the device's L2, so that the sweep streams much of it
+                          * from HBM; else GLOBAL */
   HSG_KERNEL_GLOBAL = 1, /* one thread per site, neighbours through L1/L2 (heat-bath:
                           * one thread per six-plane column, carrying its column's
                           * neighbours; the same results) */

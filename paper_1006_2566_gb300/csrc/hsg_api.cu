@@ -260,14 +260,17 @@ hsg_status check_schedule(hsg_ctx* c, const hsg_schedule* s, bool need_kind) {
 float beta_of(double T) { return std::isinf(T) ? 0.0f : (float)(1.0 / T); }
 
 // HSG_KERNEL_AUTO: the temporally blocked over-relaxation once the spins
-// and bonds (16 + 12 bytes per site) no longer fit in L2 -- it saves HBM
-// traffic, and only pays where the sweep streams from HBM (measured on
-// GB300: 1.06 x faster per OR sweep at L = 256, 1.35 x slower at L = 128,
-// whose 59 MB state stays in the 126 MB L2).
+// and bonds (16 + 12 bytes per site) exceed three quarters of L2 -- it
+// saves HBM traffic, and pays where the sweeps stream much of their state
+// from HBM.  Measured on GB300 (126 MB L2), whole sweeps of 4-hit
+// Metropolis + 1 OR sweep: L = 128 (59 MB) 73.6 against 66.4 us with the
+// global kernel, L = 144 (84 MB) 123-127 against 121-125 us, L = 152 (98
+// MB) 135-139 against 144-147 us, L = 160 157 against 167 us; at L = 256
+// one OR sweep 131.7 us against 2 x 87.9 us.
 int pick_variant(const hsg_ctx* c, int requested) {
   if (requested == HSG_KERNEL_GLOBAL || requested == HSG_KERNEL_SLAB || requested == HSG_KERNEL_WAVE) return requested;
   if (c->packed) return hsg::V_GLOBAL;
-  return 28LL * c->N > c->l2_bytes ? hsg::V_WAVE : hsg::V_GLOBAL;
+  return 4 * 28LL * c->N > 3 * c->l2_bytes ? hsg::V_WAVE : hsg::V_GLOBAL;
 }
 
 // Temporally blocked launches of one sweep under schedule s with the wave

@@ -194,14 +194,15 @@ def test_wave_full_size_l256_is_bit_identical(hsg):
     assert np.array_equal(got[1], want[1]) and len(got[1]) == 2
 
 
-def test_auto_picks_the_wave_kernel_only_beyond_l2(hsg):
+def test_auto_picks_the_wave_kernel_only_beyond_three_quarters_of_l2(hsg):
     """HSG_KERNEL_AUTO resolves to the temporally blocked sweep once the
-    28 N bytes of spins and bonds exceed L2, else to the global kernel."""
+    28 N bytes of spins and bonds exceed three quarters of L2, else to the
+    global kernel."""
     l2 = torch.cuda.get_device_properties(0).L2_cache_size
     sched = hsg.schedule(kind=hsg.HSG_HEATBATH, n_or=4)
-    for L in (16, 128, 256):
+    for L in (16, 128, 144, 152, 256):
         with hsg.Lattice(L, 1) as lat:
-            want = hsg.HSG_KERNEL_WAVE if 28 * L ** 3 > l2 else hsg.HSG_KERNEL_GLOBAL
+            want = hsg.HSG_KERNEL_WAVE if 4 * 28 * L ** 3 > 3 * l2 else hsg.HSG_KERNEL_GLOBAL
             assert hsg.hsg_kernel_for(lat.ctx, sched) == want
             for k in (hsg.HSG_KERNEL_GLOBAL, hsg.HSG_KERNEL_SLAB, hsg.HSG_KERNEL_WAVE):
                 assert hsg.hsg_kernel_for(lat.ctx, hsg.schedule(n_or=1, kernel=k)) == k
