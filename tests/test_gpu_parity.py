@@ -264,7 +264,11 @@ def test_zero_field_half_sweeps(hsg, variant):
         assert np.all(np.any(ref.reshape(-1, 3)[mask] != s64.reshape(-1, 3)[mask], axis=1))  # every site moved
 
 
-@pytest.mark.parametrize("L", [4, 8, 14, 40, 66])  # the heat-bath column march: shorter than, and ragged in, its 6-plane chunks
+# L = 4 .. 66: the heat-bath column march shorter than, and ragged in, its
+# 6-plane chunks; the slab kernel's z chunk (chosen at launch to fill the
+# GPU) is one plane up to L = 40, two at 66, and seven at 128 with a ragged
+# last chunk of two planes.
+@pytest.mark.parametrize("L", [4, 8, 14, 40, 66, 128])
 def test_kernel_variants_are_bit_identical(hsg, L):
     J = inputs.gaussian_couplings(L, seed=3)
     out = []
