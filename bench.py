@@ -228,12 +228,16 @@ def _code_only(text: str) -> str:
 
 def kernel_source_hash() -> str:
     """First 16 hex digits of the SHA-256 of the single-lattice kernels' code
-    (comments and spacing removed), which an ncu summary records to say
-    which kernels its counters belong to."""
+    (comments and spacing removed) and of the nvcc flags they are built with
+    (paths left out), which an ncu summary records to say which kernels its
+    counters belong to."""
+    from paper_1006_2566_gb300 import build as _build
+
     h = hashlib.sha256()
     for f in ("hsg_sweep.cu", "hsg_wave.cu", "hsg_device.cuh"):
         with open(os.path.join(ROOT, "paper_1006_2566_gb300", "csrc", f)) as fh:
             h.update(_code_only(fh.read()).encode())
+    h.update(" ".join(f for f in _build.NVCC_FLAGS if not os.path.isabs(f)).encode())
     return h.hexdigest()[:16]
 
 
