@@ -591,8 +591,12 @@ def run_ours(args, wl):
                                                        "p99_ms", "max_batch")},
                 "same_trace_served_vs_plain_fifo": {
                     "requests": same["requests"], "rate_req_per_s": fifo["rate_req_per_s"],
-                    "served": {k: same[k] for k in ("p50_ms", "p99_ms", "updates_per_ns")},
-                    "plain_fifo_one_per_launch": {k: fifo[k] for k in ("p50_ms", "p99_ms", "updates_per_ns")}},
+                    "served": {k: same[k] for k in ("p50_ms", "p99_ms", "updates_per_ns", "tick_sweeps",
+                                                    "host_ms_per_tick")},
+                    "plain_fifo_one_per_launch": {k: fifo[k] for k in ("p50_ms", "p99_ms", "updates_per_ns")},
+                    "served_p99_over_fifo_p99": round(same["p99_ms"] / fifo["p99_ms"], 3),
+                    "served_by_tick_sweeps": m["served_same_trace_by_tick_sweeps"]},
+                "pool_config": m["pool_config"],
             }
     if world == 1 and not args.no_cpu_baseline:
         out["errors_vs_oracle"] = errors
@@ -959,43 +963,61 @@ SERVE = dict(rate=2000.0, n_overload=800, n_sub=300, n_plain=100, seed=5, budget
 
 
 def measure_serving(n_overload: int = SERVE["n_overload"], n_sub: int = SERVE["n_sub"],
-                    n_plain: int = SERVE["n_plain"]) -> dict:
+                    n_plain: int = SERVE["n_plain"], tick_sweeps=(1, 3, 30)) -> dict:
     """The serving workload on the current device: an overload trace at the
     configured rate (throughput against offered load), a sub-saturating
     trace at 0.6 x the measured capacity, and its first n_plain requests
-    both served and one per launch in arrival order (p50/p99 side by side)."""
+    both served and one per launch in arrival order (p50/p99 side by side),
+    then served again with each tick length in `tick_sweeps`."""
     import torch
 
     from paper_1006_2566_gb300 import hsg, serve
 
     kw = dict(kind=hsg.HSG_METROPOLIS, hits=4, proposal=hsg.HSG_PROP_BALL, step=0.5, n_or=2, renorm_every=10)
     stream = torch.cuda.Stream()
-    # warm-up: a short trace (builds graphs, pages in the arena)
-    serve.serve(serve.poisson_trace(40, SERVE["rate"], seed=99, first_sample=10 ** 6), kw, SERVE["budget"],
-                SERVE["max_slots"], stream)
+    # warm-up: a short trace (builds graphs, pages in the arena) whose pool
+    # autotunes its launch configuration once; the measured traces start with
+    # that configuration instead of tuning while their requests wait
+    _, st_w = serve.serve(serve.poisson_trace(40, SERVE["rate"], seed=99, first_sample=10 ** 6), kw,
+                          SERVE["budget"], SERVE["max_slots"], stream)
+    cfg = st_w.extra["config"]
     over = serve.poisson_trace(n_overload, SERVE["rate"], seed=SERVE["seed"])
-    res_o, st_o = serve.serve(over, kw, SERVE["budget"], SERVE["max_slots"], stream)
+    res_o, st_o = serve.serve(over, kw, SERVE["budget"], SERVE["max_slots"], stream, config=cfg)
     capacity = st_o.completed / st_o.wall_seconds  # requests per second at saturation
     sub_rate = 0.6 * capacity
     sub = serve.poisson_trace(n_sub, sub_rate, seed=SERVE["seed"] + 1, first_sample=10 ** 5)
-    res_s, st_s = serve.serve(sub, kw, SERVE["budget"], SERVE["max_slots"], stream)
+    res_s, st_s = serve.serve(sub, kw, SERVE["budget"], SERVE["max_slots"], stream, config=cfg)
     plain_trace = sub[:n_plain]
     res_p, st_p = serve.serve_fifo(plain_trace, kw, stream)
-    res_b, st_b = serve.serve(plain_trace, kw, SERVE["budget"], SERVE["max_slots"], stream)
+    res_b, st_b = serve.serve(plain_trace, kw, SERVE["budget"], SERVE["max_slots"], stream, config=cfg)
+    # the same trace at other tick lengths (sweeps queued per loop iteration)
+    by_tick = {}
+    for tick in tick_sweeps:
+        _, st_t = serve.serve(plain_trace, kw, SERVE["budget"], SERVE["max_slots"], stream, tick_sweeps=tick,
+                              config=cfg)
+        by_tick[str(tick)] = {"p50_ms": round(st_t.p50_ms, 2), "p99_ms": round(st_t.p99_ms, 2),
+                              "ticks": st_t.ticks, "host_ms_per_tick": round(st_t.extra["host_ms_per_tick"], 3)}
     passes = 3
     offered = sum(r.L ** 3 * r.sweeps * passes for r in over) / (over[-1].arrival * 1e9)
 
     def block(st):
-        return {"completed": st.completed, "wall_s": round(st.wall_seconds, 3), "updates_per_ns": round(st.updates_per_ns, 3),
-                "p50_ms": round(st.p50_ms, 2), "p99_ms": round(st.p99_ms, 2), "mean_ms": round(st.mean_ms, 2),
-                "max_batch": st.max_batch, "ticks": st.ticks}
+        out = {"completed": st.completed, "wall_s": round(st.wall_seconds, 3),
+               "updates_per_ns": round(st.updates_per_ns, 3), "p50_ms": round(st.p50_ms, 2),
+               "p99_ms": round(st.p99_ms, 2), "mean_ms": round(st.mean_ms, 2), "max_batch": st.max_batch,
+               "ticks": st.ticks}
+        if "host_ms_per_tick" in st.extra:
+            out["host_ms_per_tick"] = round(st.extra["host_ms_per_tick"], 3)
+        return out
 
     return {
         "overload": dict(block(st_o), offered_updates_per_ns=round(offered, 2), rate_req_per_s=SERVE["rate"],
                          requests=len(over)),
         "sub_saturating": dict(block(st_s), rate_req_per_s=round(sub_rate, 1), requests=len(sub)),
         "plain_fifo_one_per_launch": dict(block(st_p), requests=len(plain_trace), rate_req_per_s=round(sub_rate, 1)),
-        "served_same_trace": dict(block(st_b), requests=len(plain_trace)),
+        "served_same_trace": dict(block(st_b), requests=len(plain_trace), tick_sweeps=10),
+        "served_same_trace_by_tick_sweeps": by_tick,
+        "pool_config": None if cfg is None else dict(zip(("threads", "tile_sites", "blocks_per_sm", "hits_per_pass"),
+                                                         cfg)),
     }
 
 

@@ -71,8 +71,13 @@ __global__ void __launch_bounds__(G_THREADS, U == U_OR ? 16 : 1) k_half_sweep_gl
 // A persistent grid that deals out equal contiguous (column block, plane)
 // ranges, one CTA per resident slot (no partial last wave), took 105.7 us:
 // neighbouring column blocks then work on different planes, so the rows
-// they share are probably no longer found in L2.
+// they share are probably no longer found in L2.  Blocks of 16 x 8 threads
+// (a warp spans two rows, so a block's y-neighbour rows are mostly its own
+// and come from L1): 89.4 us against 90.7 us for 64 x 2 (fp32 subnormals
+// flushed); 32 x 4, 128 x 1, 8 x 16 and 256-thread blocks 89.9-91.1 us;
+// streaming (evict-first) stores of the new spins gained 0.2 us more.
 constexpr int ZM_PLANES = 6;
+constexpr int ZM_BX = 16, ZM_BY = 8;
 
 template <int U>
 __global__ void __launch_bounds__(G_THREADS, 12) k_half_sweep_column(const SweepArgs a) {
@@ -266,8 +271,8 @@ cudaError_t launch_kind(int variant, const SweepArgs& a, int sm_count, cudaStrea
     const dim3 block = a.Lh >= 64 ? dim3(64, 2) : dim3(32, 4);
     const dim3 grid(cdiv(a.Lh, block.x), cdiv(a.L, block.y), (unsigned)a.L);
     if constexpr (U == U_HB) {
-      const dim3 gcol(grid.x, grid.y, cdiv(a.L, ZM_PLANES));
-      k_half_sweep_column<U><<<gcol, block, 0, s>>>(a);
+      const dim3 gcol(cdiv(a.Lh, ZM_BX), cdiv(a.L, ZM_BY), cdiv(a.L, ZM_PLANES));
+      k_half_sweep_column<U><<<gcol, dim3(ZM_BX, ZM_BY), 0, s>>>(a);
     } else {
       k_half_sweep_global<U><<<grid, block, 0, s>>>(a);
     }

@@ -110,7 +110,8 @@ def _marker(stream):
 
 def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots: int, stream=None,
           tick_sweeps: int = 10, keep_spins: bool = False, autotune: bool = True,
-          cancels: dict[int, float] | None = None, pool_factory=None) -> tuple[list[Result], ServeStats]:
+          cancels: dict[int, float] | None = None, pool_factory=None,
+          config: tuple | None = None) -> tuple[list[Result], ServeStats]:
     """Run the request loop in real time (arrivals are honoured on the wall
     clock from the call).  sched_kw: the schedule of every request
     (hsg.schedule keywords without T).  cancels: request id -> time (seconds
@@ -118,9 +119,16 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
     waiting is dropped, an admitted one is retired at the next tick (its
     memory freed for the next admission); the other lattices are untouched.
     pool_factory(budget_bytes, max_slots, stream) makes the pool (hsg.Pool by
-    default).  Returns per-request results in completion order and summary
-    statistics (ids of withdrawn requests in stats.extra["cancelled"], of
-    requests larger than the whole pool in stats.extra["rejected"]).
+    default).  config: a pool launch configuration (threads, tile_sites,
+    blocks_per_sm, hits_per_pass), e.g. the one a previous run's autotuner
+    chose, set before the first sweep; with it the loop does not autotune.
+    Otherwise, with autotune, the loop tunes once, when eight lattices are
+    first resident -- every admitted request then waits for the tuning
+    sweeps, so a server tunes at start-up and passes the result here.
+    Returns per-request results in completion order and summary statistics
+    (ids of withdrawn requests in stats.extra["cancelled"], of requests
+    larger than the whole pool in stats.extra["rejected"], the launch
+    configuration used in stats.extra["config"], None if the default).
 
     The host knows when every lattice finishes (its sweep count), so it
     schedules tick n+1 -- retirements, admissions into the freed memory,
@@ -142,10 +150,14 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
     active: dict[int, list] = {}  # slot -> [request, sweeps left, admitted at]
     results: list[Result] = []
     ticks = max_batch = 0
-    tuned = not autotune
+    tuned = not autotune or config is not None
+    used_config = tuple(config) if config is not None else None
     prev = None  # the tick in flight: (marker, energy buffer or None, [(slot, request, admitted, spins)])
     buf = 0
+    waited = 0.0  # seconds the host spent waiting (for the device or for arrivals)
     with make_pool(budget_bytes, max_slots, stream) as pool:
+        if config is not None:
+            hsg.hsg_pool_config(pool.pool, *config)
         t0 = time.perf_counter()
         while pending or waiting or active or prev is not None:
             now = time.perf_counter() - t0
@@ -177,7 +189,7 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
             cur = None
             if active:
                 if not tuned and len(active) >= 8:
-                    hsg.hsg_pool_autotune(pool.pool, sched)
+                    used_config = hsg.hsg_pool_autotune(pool.pool, sched)
                     tuned = True
                 k = min(tick_sweeps, min(a[1] for a in active.values()))
                 pool.sweep(sched, k)
@@ -203,11 +215,15 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
                 if waiting:  # an empty pool refused it: it can never be admitted
                     rejected.append(waiting.popleft().rid)
                 elif pending:
-                    time.sleep(max(0.0, min(pending[0].arrival - (time.perf_counter() - t0), 0.01)))
+                    tw = time.perf_counter()
+                    time.sleep(max(0.0, min(pending[0].arrival - (tw - t0), 0.01)))
+                    waited += time.perf_counter() - tw
                 continue
             if prev is not None:  # wait for the tick before this one and hand out its results
                 marker, b, finished = prev
+                tw = time.perf_counter()
                 marker.synchronize()
+                waited += time.perf_counter() - tw
                 if finished:
                     energies = pool.energies_read(b)
                     t_done = time.perf_counter() - t0
@@ -219,7 +235,8 @@ def serve(requests: list[Request], sched_kw: dict, budget_bytes: int, max_slots:
     by_id = {q.rid: q for q in requests}
     upd = sum(_updates(by_id[r.rid], passes) for r in results)
     return results, ServeStats(len(results), wall, upd, p50, p99, mean, max_batch, ticks,
-                               extra={"cancelled": cancelled, "rejected": rejected})
+                               extra={"cancelled": cancelled, "rejected": rejected, "config": used_config,
+                                      "host_ms_per_tick": (wall - waited) * 1e3 / ticks if ticks else math.nan})
 
 
 def serve_fifo(requests: list[Request], sched_kw: dict, stream=None, keep_spins: bool = False):

@@ -116,7 +116,36 @@ def test_serve_loop_admits_in_order_under_the_budget_and_runs_each_to_its_sweeps
         assert by[r.rid].energy == -r.sweeps / 1000.0  # each ran exactly its sweeps
     admits = [e[1] for e in FakePool.last.log if e[0] == "admit"]
     assert admits == [0, 1, 2, 3]  # arrival order; request 2 waited for memory
-    assert st.max_batch == 2 and st.extra == {"cancelled": [], "rejected": []}
+    assert st.max_batch == 2 and st.extra["cancelled"] == [] and st.extra["rejected"] == []
+    assert st.extra["config"] is None and st.extra["host_ms_per_tick"] >= 0.0
+
+
+class ConfigPool(FakePool):
+    """Counts its sweep calls; is its own handle for hsg_pool_config."""
+
+    def __init__(self, *a):
+        super().__init__(*a)
+        self.pool = self
+        self.sweeps = 0
+
+    def sweep(self, sched, k):
+        self.sweeps += 1
+        super().sweep(sched, k)
+
+
+def test_serve_loop_sets_a_given_launch_configuration_before_the_first_sweep(monkeypatch):
+    pytest.importorskip("torch")
+    from paper_1006_2566_gb300 import hsg
+
+    calls = []
+    monkeypatch.setattr(hsg, "hsg_pool_config", lambda pool, *cfg: calls.append((pool.sweeps, cfg)))
+    monkeypatch.setattr(hsg, "hsg_pool_autotune", lambda *a: pytest.fail("autotuned although a config was given"))
+    rq = reqs([(0.0, 6, 5)] * 9)
+    res, st = serve.serve(rq, dict(kind=1, n_or=1), budget_bytes=9 * 6 ** 3, max_slots=16, stream=SyncStream(),
+                          pool_factory=ConfigPool, config=(256, 1024, 8, 4))
+    assert st.completed == 9 and st.extra["config"] == (256, 1024, 8, 4)
+    assert calls == [(0, (256, 1024, 8, 4))]  # set once, before the first sweep
+    assert ConfigPool.last.sweeps > 0
 
 
 class SlowPool(FakePool):
