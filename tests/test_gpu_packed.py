@@ -13,6 +13,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 import oracle  # noqa: E402
+import parity_rules  # noqa: E402
 from paper_1006_2566_gb300 import inputs  # noqa: E402
 
 
@@ -67,20 +68,24 @@ def test_packed_graph_replay_and_uploaded_spins(hsg):
 
 
 def test_packed_half_sweep_matches_oracle(hsg):
-    """One OR half-sweep of a packed lattice against the oracle (the
-    tolerance rule of test_gpu_parity for a well-conditioned field)."""
+    """Over-relaxation and heat-bath half-sweeps of a packed lattice, both
+    colours, against the oracle layer by layer under the parity rules of
+    the float4 tests (every site within 1e-5, the other colour unchanged)."""
     L = 16
     J = inputs.gaussian_couplings(L, seed=5)
+    Jr = inputs.round_to_f32(J)
     s32 = inputs.random_spins(L, seed=6, dtype=np.float32)
+    params = oracle.Params(key=oracle.key(1), beta=1.0 / 0.5)
     with hsg.Lattice(L, 1, layout=hsg.HSG_LAYOUT_PACKED) as lat:
         lat.set_couplings(J)
         lat.set_spins(s32)
-        lat.half_sweep(hsg.schedule(), hsg.HSG_OVERRELAX, 0)
-        got = lat.spins().astype(np.float64)
-    ref = s32.astype(np.float64)
-    oracle.half_sweep(L, inputs.round_to_f32(J), ref, oracle.OR, 0, oracle.Params())
-    err = np.max(np.abs(got - ref).reshape(-1, 3), axis=1)
-    assert np.mean(err <= 1e-5) >= 0.999 and np.max(err) <= 1e-3
+        before = lat.spins()
+        for upd, kind in ((oracle.OR, hsg.HSG_OVERRELAX), (oracle.HB, hsg.HSG_HEATBATH)):
+            for colour in (0, 1):
+                lat.half_sweep(hsg.schedule(T=0.5), kind, colour)
+                after = lat.spins()
+                parity_rules.check_layer(L, Jr, before, after, upd, colour, params, label=f"packed {upd} c{colour}")
+                before = after
 
 
 def test_packed_layout_rejects_staged_kernels(hsg):
