@@ -127,6 +127,10 @@ __device__ __forceinline__ float3 update_metropolis(float3 s, float3 h, uint32_t
 // frame of h/|h| built as in Duff et al., "Building an Orthonormal Basis,
 // Revisited" (JCGT 2017).  Uniform on S^2 when x < 1e-6.
 //
+// Where s = 1 - cos(theta) > 1 (the lower hemisphere about h), the branch
+// below takes 2 - s from its own exact form instead of subtracting, so that
+// sin(theta) keeps relative precision up to cos(theta) = -1.
+//
 // fp32 evaluation of log(1 + v): where 1 + v >= 1/2, w = 1 + v rounded and
 // log1p(v) = v log(w)/(w - 1) (Goldberg, "What every computer scientist
 // should know about floating-point arithmetic", 1991, Theorem 4: relative
@@ -160,8 +164,16 @@ __device__ __forceinline__ float3 update_heatbath(float3 h, uint32_t site, uint3
   if (near_one) lg = (w == 1.0f) ? v : lg * __fdividef(v, w - 1.0f);
   float sv = __fdividef(-lg, x);
   sv = fminf(fmaxf(sv, 0.0f), 2.0f);
-  const float ct = 1.0f - sv;
-  const float t = sv * (2.0f - sv);
+  float ct = 1.0f - sv, t = sv * (2.0f - sv);
+  if (sv > 1.0f && x < 16.0f) {
+    // Near cos(theta) = -1, 2 - s formed as 2 - sv cancels and sin(theta) =
+    // sqrt(s (2 - s)) inherits the cancellation.  There 2 - s comes from the
+    // exact identity 2 - s = log(1 + (1 - u0) (e^{2x} - 1)) / x to relative
+    // precision (s > 1 needs -log(1 - u0) > x, so x < 16.7: e^{2x} is finite).
+    const float d = fminf(fmaxf(__fdividef(log1pf((1.0f - u0) * expm1f(2.0f * x)), x), 0.0f), 2.0f);
+    ct = d - 1.0f;
+    t = (2.0f - d) * d;
+  }
   const float st = t > 0.0f ? t * rsqrtf(t) : 0.0f;
   float sp, cp;
   __sincosf(6.283185307179586f * (u1 - 0.5f), &sp, &cp);  // angle 2 pi u1 - pi

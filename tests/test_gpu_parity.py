@@ -214,7 +214,8 @@ def test_fused_long_run_energy_statistics_match_oracle(hsg):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
-@pytest.mark.parametrize("L,T", [(6, 1.0), (16, 0.3), (40, 0.3), (66, 1.0), (16, math.inf), (16, 0.01)])
+@pytest.mark.parametrize("L,T", [(6, 1.0), (16, 0.3), (40, 0.3), (66, 1.0), (16, math.inf), (16, 0.01), (40, 3.0),
+                                 (66, 10.0), (40, 100.0)])
 def test_heatbath_half_sweep_parity(hsg, variant, L, T):
     J, s32 = oracle_state(L, 500 + L, 600 + L)
     Jr = inputs.round_to_f32(J)
